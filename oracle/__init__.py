@@ -1,0 +1,205 @@
+"""FP64 CPU oracle for the ENUFFT type-1 transform, EMS and gradient (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use this
+package; the CUDA library never imports, links or calls it, and it shares no code with the
+library.  The arithmetic lives in ``enufft_oracle.c`` (plain C, FP64, direct sums, one function
+per passage of the paper); this module compiles it with gcc and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "enufft_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, OpenMP, no FP contraction so binary32 steps round as written)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i64, i32, vp = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        _lib.oracle_frame.argtypes = [i32, vp, d, i32, vp]
+        _lib.oracle_window.argtypes = [i32, vp, d, i32, i64, vp, vp, vp]
+        _lib.oracle_type1_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, i32]
+        _lib.oracle_type1_backward_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp,
+                                                     vp, vp, i32]
+        _lib.oracle_ems_batch.argtypes = [i64, i32, vp, vp, i32, i32, i32, d, d, d, d, d, i32, i32, i32,
+                                          vp, vp, vp, vp, i32]
+        _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, vp, vp, vp, vp]
+        _lib.oracle_ems_grad_coeffs.argtypes = [i64, i32, vp, vp, i32, i32, vp, vp, vp, vp]
+        for f in ("oracle_frame", "oracle_window", "oracle_type1_batch", "oracle_type1_backward_batch",
+                  "oracle_ems_batch", "oracle_ems_energies", "oracle_ems_grad_coeffs",
+                  "oracle_threads_used"):
+            getattr(_lib, f).restype = ctypes.c_int
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _arr(a, dt) -> np.ndarray:
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class EMSParams:
+    """Sec. 2.2 parameters; defaults are the values of the paper's EMS illustration."""
+    k_min: int = 1
+    k_max: int = 12
+    alpha_min: float = 0.0
+    alpha_max: float = 0.7
+    delta: float = 0.02
+    w1: float = 0.5
+    w2: float = 0.5
+    sum_all: int = 0      # 0 HEAD reading (sums over J_max = min(J*, K_max)), 1 ALL reading (J*)
+    include_dc: int = 0
+
+
+def frame(nverts: int, verts, eta: float = 1.5, mask: int = 0) -> dict:
+    out = np.zeros(5)
+    v = _f64(verts).reshape(-1)
+    assert lib().oracle_frame(int(nverts), _p(v), float(eta), int(mask), _p(out)) == 0
+    return dict(cx=out[0], cy=out[1], H=out[2], L=out[3], area=out[4])
+
+
+def window(nverts: int, verts, x, y, eta: float = 1.5, mask: int = 0) -> np.ndarray:
+    v = _f64(verts).reshape(-1)
+    x, y = _f64(x), _f64(y)
+    win = np.zeros(len(x), dtype=np.int32)
+    assert lib().oracle_window(int(nverts), _p(v), float(eta), int(mask), len(x), _p(x), _p(y), _p(win)) == 0
+    return win
+
+
+def _cells(wl):
+    off = _arr(wl.offsets, np.int64)
+    nv = _arr(wl.nverts, np.int32)
+    vv = _f64(wl.verts).reshape(len(nv), 12)
+    return off, nv, vv
+
+
+def type1(wl, nthreads: int = 0, P: int | None = None) -> np.ndarray:
+    """Coefficients [n_cells, P, P] complex128, index [cell, n + P/2, m + P/2] (App. B sum)."""
+    P = P or wl.modes
+    off, nv, vv = _cells(wl)
+    x, y, h, w = (_f64(a) for a in (wl.x, wl.y, wl.h, wl.w))
+    out = np.zeros((len(nv), P, P, 2))
+    r = lib().oracle_type1_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w), int(P),
+                                 float(wl.eta), int(wl.mask), _p(out), int(nthreads))
+    assert r == 0, "oracle_type1_batch failed"
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def threads_used() -> int:
+    return lib().oracle_threads_used()
+
+
+def type1_backward(wl, G: np.ndarray, nthreads: int = 0):
+    """(dL/dh, dL/dw) for G = dL/dRe(coeffs) + i dL/dIm(coeffs), shape [n_cells, P, P]."""
+    P = wl.modes
+    off, nv, vv = _cells(wl)
+    x, y, h, w = (_f64(a) for a in (wl.x, wl.y, wl.h, wl.w))
+    g = np.ascontiguousarray(np.stack([G.real, G.imag], -1), dtype=np.float64)
+    gh = np.zeros(len(x)); gw = np.zeros(len(x))
+    r = lib().oracle_type1_backward_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w),
+                                          int(P), float(wl.eta), int(wl.mask), _p(g), _p(gh), _p(gw),
+                                          int(nthreads))
+    assert r == 0
+    return gh, gw
+
+
+def ems(coeffs: np.ndarray, params: EMSParams = EMSParams(), mode_weights=None, energy_fp32: bool = False,
+        nthreads: int = 0):
+    """EMS per spectrum.  Returns (kstar[n], sel[n, K_max] pair indices (-1 padded),
+    retained_power[n], diag[n, 10])."""
+    coeffs = np.asarray(coeffs)
+    n, P, _ = coeffs.shape
+    c = np.ascontiguousarray(np.stack([coeffs.real, coeffs.imag], -1), dtype=np.float64)
+    W = None
+    per_cell = 0
+    if mode_weights is not None:
+        W = _f64(mode_weights)
+        per_cell = int(W.ndim == 3)
+    ks = np.zeros(n, dtype=np.int32)
+    sel = np.zeros((n, params.k_max), dtype=np.int32)
+    ret = np.zeros(n)
+    diag = np.zeros((n, 10))
+    r = lib().oracle_ems_batch(n, P, _p(c), _p(W) if W is not None else None, per_cell, params.k_min,
+                               params.k_max, params.alpha_min, params.alpha_max, params.delta, params.w1,
+                               params.w2, params.sum_all, params.include_dc, int(energy_fp32), _p(ks),
+                               _p(sel), _p(ret), _p(diag), int(nthreads))
+    assert r == 0
+    return ks, sel, ret, diag
+
+
+def ems_energies(E, params: EMSParams = EMSParams()):
+    """EMS on an explicit energy list.  Returns (K*, selected positions, retained, diag[6])."""
+    E = _f64(E)
+    ks = np.zeros(1, dtype=np.int32)
+    sel = np.zeros(params.k_max, dtype=np.int32)
+    ret = np.zeros(1)
+    diag = np.zeros(10)
+    r = lib().oracle_ems_energies(len(E), _p(E), params.k_min, params.k_max, params.alpha_min,
+                                  params.alpha_max, params.delta, params.w1, params.w2, params.sum_all,
+                                  _p(ks), _p(sel), _p(ret), _p(diag))
+    assert r == 0
+    return int(ks[0]), sel[: int(ks[0])].copy(), float(ret[0]), diag[:6].copy()
+
+
+def ems_grad_coeffs(coeffs, kstar, sel, grad_power, k_max: int, mode_weights=None) -> np.ndarray:
+    """G = grad_power_j * d(retained power_j)/d(coeffs) with the selection held fixed."""
+    coeffs = np.asarray(coeffs)
+    n, P, _ = coeffs.shape
+    c = np.ascontiguousarray(np.stack([coeffs.real, coeffs.imag], -1), dtype=np.float64)
+    W = _f64(mode_weights) if mode_weights is not None else None
+    per_cell = int(W is not None and W.ndim == 3)
+    G = np.zeros((n, P, P, 2))
+    ks = _arr(kstar, np.int32); sl = _arr(sel, np.int32); gp = _f64(grad_power)
+    lib().oracle_ems_grad_coeffs(n, P, _p(c), _p(W) if W is not None else None, per_cell, int(k_max),
+                                 _p(ks), _p(sl), _p(gp), _p(G))
+    return G[..., 0] + 1j * G[..., 1]
+
+
+def selected_power(coeffs, kstar, sel, k_max: int, mode_weights=None) -> np.ndarray:
+    """P_j = sum over the selected pairs of W_p (|h_p|^2 + |h_-p|^2) (DC pair counted once)."""
+    coeffs = np.asarray(coeffs)
+    n, P, _ = coeffs.shape
+    half = P // 2
+    out = np.zeros(n)
+    for j in range(n):
+        for k in range(int(kstar[j])):
+            p = int(sel[j][k])
+            m, nn = p % P - half, p // P - half
+            wt = 1.0 if mode_weights is None else float(np.asarray(mode_weights).reshape(-1, P, P)[
+                j if np.asarray(mode_weights).ndim == 3 else 0][nn + half, m + half])
+            e = abs(coeffs[j, nn + half, m + half]) ** 2
+            if (m, nn) != (0, 0):
+                e += abs(coeffs[j, -nn + half, -m + half]) ** 2
+            out[j] += wt * e
+    return out

@@ -1,0 +1,465 @@
+/*
+ * enufft_oracle.c -- TEST INFRASTRUCTURE, not product code.
+ *
+ * A plain, slow, FP64 CPU statement of what the ENUFFT hot path computes, written from the
+ * paper (arxiv 2606.21278) and used only by the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark.  It shares no code, header, table or helper with the CUDA
+ * library: every quantity is evaluated here directly from its definition.
+ *
+ *   frame       App. A  (centroid, centroid-aligned frame R = I, half-width H, square B,
+ *                        shifted coordinates x' = u + H, masks D = B n {square, cell, circle})
+ *   |D|         App. A/B (area of the active quadrature domain)
+ *   type-1      App. B, Eq. "discrete_quadrature":  h_mn = 1/|D| sum_q w_q h_q e^{-i(k_m x'_q + k_n y'_q)},
+ *               k_m = 2 pi m / L, L = 2H, evaluated by direct summation (the NUFFT of Sec. 2.1.2 is a
+ *               fast evaluation of exactly this sum)
+ *   EMS         Sec. 2.2, Eqs. "energy", "weighted_e", "sorted_energy", "n_eff", "s_delta", "c_score",
+ *               "alpha_c", "f_cum", "k_elastic" (+ the footnote bounding all sums by J_max)
+ *   gradient    derivative of the EMS-retained power with the selected set held fixed; it is the
+ *               adjoint (type-2 sum) of the quadrature above
+ *
+ * Readings where the paper is silent (documented with the build):
+ *   - mode box m, n in [-P/2, P/2); EMS candidates are mode pairs +-(m,n) with |m|,|n| <= P/2-1,
+ *     represented by the half-plane member (n > 0, or n == 0 and m > 0); DC excluded by default;
+ *   - sort ties are broken by ascending pair index p = (n + P/2) P + (m + P/2);
+ *   - J_max < 2 gives S_delta = 0; a gap with E_(j+1) = 0 contributes 0; total power 0 gives K* = 0;
+ *     K* never exceeds the number of pairs with positive energy;
+ *   - HEAD reading (default): N_eff and the denominator of theta use the top J_max = min(J*, K_max)
+ *     energies; ALL reading: they use all J* energies;
+ *   - hexagon (and any convex polygon) centroid = mean of its vertices, as for triangles.
+ *
+ * Parity status: every function here is pinned by closed-form or library checks in the tests
+ * (regular-grid DFT, plane wave statistics, Gibbs step, polygon Fourier transform, DC term,
+ * App. D limits of N_eff / S_delta, finite differences); none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* ----------------------------------------------------------------------------------------- */
+/* App. A: local window                                                                        */
+/* ----------------------------------------------------------------------------------------- */
+
+typedef struct {
+    double cx, cy;   /* centroid x-bar                                  */
+    double H;        /* half-width of the square spectral domain B      */
+    double L;        /* period L = 2H                                   */
+    double area;     /* |D|, area of the active quadrature domain       */
+    int nv;          /* polygon vertex count                            */
+    double ux[8], uy[8]; /* polygon vertices in the centred frame u = x - x-bar (R = I) */
+    double orient;   /* +1 counter-clockwise, -1 clockwise              */
+    int mask;        /* 0 cell (B n polygon), 1 square (B), 2 circle (B n disk of radius H) */
+} oframe;
+
+/* Area of a polygon by the shoelace formula (absolute value). */
+static double shoelace(int n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        s += x[i] * y[j] - x[j] * y[i];
+    }
+    return 0.5 * fabs(s);
+}
+
+/* Clip a polygon by the half-plane  s * coord(axis) <= H  (Sutherland-Hodgman, one edge). */
+static int clip_halfplane(int n, const double *x, const double *y, int axis, double s, double H,
+                          double *ox, double *oy) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        double ci = s * (axis == 0 ? x[i] : y[i]) - H;
+        double cj = s * (axis == 0 ? x[j] : y[j]) - H;
+        int in_i = ci <= 0.0, in_j = cj <= 0.0;
+        if (in_i) { ox[m] = x[i]; oy[m] = y[i]; ++m; }
+        if (in_i != in_j) {
+            double t = ci / (ci - cj);
+            ox[m] = x[i] + t * (x[j] - x[i]);
+            oy[m] = y[i] + t * (y[j] - y[i]);
+            ++m;
+        }
+    }
+    return m;
+}
+
+/* Frame of one cell (App. A): centroid, centroid-aligned frame, H = (eta/2) max extent,
+ * B = [-H, H]^2, and |D| for the chosen mask.  Returns 0, or -1 for a bad polygon. */
+static int frame_of(int nv, const double *v, double eta, int mask, oframe *f) {
+    if (nv < 3 || nv > 6) return -1;
+    memset(f, 0, sizeof(*f));
+    f->nv = nv;
+    f->mask = mask;
+    for (int i = 0; i < nv; ++i) { f->cx += v[2 * i]; f->cy += v[2 * i + 1]; }
+    f->cx /= nv;
+    f->cy /= nv;
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int i = 0; i < nv; ++i) {
+        f->ux[i] = v[2 * i] - f->cx;
+        f->uy[i] = v[2 * i + 1] - f->cy;
+        if (f->ux[i] < xmin) xmin = f->ux[i];
+        if (f->ux[i] > xmax) xmax = f->ux[i];
+        if (f->uy[i] < ymin) ymin = f->uy[i];
+        if (f->uy[i] > ymax) ymax = f->uy[i];
+    }
+    double ext = (xmax - xmin) > (ymax - ymin) ? (xmax - xmin) : (ymax - ymin);
+    f->H = 0.5 * eta * ext;
+    f->L = 2.0 * f->H;
+    double sa = 0.0;
+    for (int i = 0; i < nv; ++i) {
+        int j = (i + 1) % nv;
+        sa += f->ux[i] * f->uy[j] - f->ux[j] * f->uy[i];
+    }
+    f->orient = sa >= 0.0 ? 1.0 : -1.0;
+    if (mask == 1) {
+        f->area = f->L * f->L;
+    } else if (mask == 2) {
+        f->area = ORACLE_PI * f->H * f->H;
+    } else {
+        /* D = B n cell: clip the polygon by the four sides of B, then shoelace */
+        double ax[32], ay[32], bx[32], by[32];
+        int n = nv;
+        for (int i = 0; i < nv; ++i) { ax[i] = f->ux[i]; ay[i] = f->uy[i]; }
+        n = clip_halfplane(n, ax, ay, 0, +1.0, f->H, bx, by);
+        n = clip_halfplane(n, bx, by, 0, -1.0, f->H, ax, ay);
+        n = clip_halfplane(n, ax, ay, 1, +1.0, f->H, bx, by);
+        n = clip_halfplane(n, bx, by, 1, -1.0, f->H, ax, ay);
+        f->area = n >= 3 ? shoelace(n, ax, ay) : 0.0;
+    }
+    return 0;
+}
+
+/* Window indicator of a sample (App. A masks, closed sets). */
+static int in_window(const oframe *f, double x, double y) {
+    double ux = x - f->cx, uy = y - f->cy;
+    if (ux < -f->H || ux > f->H || uy < -f->H || uy > f->H) return 0; /* outside B */
+    if (f->mask == 1) return 1;
+    if (f->mask == 2) return ux * ux + uy * uy <= f->H * f->H;
+    for (int i = 0; i < f->nv; ++i) {
+        int j = (i + 1) % f->nv;
+        double cr = (f->ux[j] - f->ux[i]) * (uy - f->uy[i]) - (f->uy[j] - f->uy[i]) * (ux - f->ux[i]);
+        if (f->orient * cr < 0.0) return 0;
+    }
+    return 1;
+}
+
+/* Exported: frame constants of one cell: out = {cx, cy, H, L, |D|}. */
+int oracle_frame(int nv, const double *verts, double eta, int mask, double *out) {
+    oframe f;
+    if (frame_of(nv, verts, eta, mask, &f)) return -1;
+    out[0] = f.cx; out[1] = f.cy; out[2] = f.H; out[3] = f.L; out[4] = f.area;
+    return 0;
+}
+
+/* Exported: window indicator for Q samples of one cell. */
+int oracle_window(int nv, const double *verts, double eta, int mask, int64_t Q, const double *x,
+                  const double *y, int32_t *win) {
+    oframe f;
+    if (frame_of(nv, verts, eta, mask, &f)) return -1;
+    for (int64_t q = 0; q < Q; ++q) win[q] = in_window(&f, x[q], y[q]);
+    return 0;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* App. B, Eq. discrete_quadrature: direct FP64 type-1 sum                                     */
+/* ----------------------------------------------------------------------------------------- */
+
+/* One cell. coeffs[(n + P/2) * P + (m + P/2)] = (re, im), m, n in [-P/2, P/2). */
+static int type1_cell(const oframe *f, int P, int64_t Q, const double *x, const double *y,
+                      const double *h, const double *w, double *coeffs) {
+    int half = P / 2;
+    double *ex = (double *)malloc(sizeof(double) * 2 * P);
+    double *ey = (double *)malloc(sizeof(double) * 2 * P);
+    if (!ex || !ey) { free(ex); free(ey); return -2; }
+    memset(coeffs, 0, sizeof(double) * 2 * (size_t)P * P);
+    for (int64_t q = 0; q < Q; ++q) {
+        if (!in_window(f, x[q], y[q])) continue;
+        double c = w[q] * h[q] / f->area;             /* w_q h_q / |D| */
+        double xp = (x[q] - f->cx) + f->H;            /* x' = u_x + H  */
+        double yp = (y[q] - f->cy) + f->H;
+        for (int i = 0; i < P; ++i) {
+            double k = 2.0 * ORACLE_PI * (double)(i - half) / f->L;   /* k_m = 2 pi m / L */
+            ex[2 * i] = cos(k * xp);
+            ex[2 * i + 1] = -sin(k * xp);
+            ey[2 * i] = cos(k * yp);
+            ey[2 * i + 1] = -sin(k * yp);
+        }
+        for (int in = 0; in < P; ++in) {
+            double byr = c * ey[2 * in], byi = c * ey[2 * in + 1];
+            double *row = coeffs + 2 * (size_t)in * P;
+            for (int im = 0; im < P; ++im) {
+                double axr = ex[2 * im], axi = ex[2 * im + 1];
+                row[2 * im] += axr * byr - axi * byi;       /* e^{-i k_m x'} e^{-i k_n y'} */
+                row[2 * im + 1] += axr * byi + axi * byr;
+            }
+        }
+    }
+    free(ex);
+    free(ey);
+    return 0;
+}
+
+static int nthreads_used = 1;
+
+/* Exported: batched type-1 over cells (CSR offsets), OpenMP over cells. */
+int oracle_type1_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
+                       const double *verts /* n_cells * 12 */, const double *x, const double *y,
+                       const double *h, const double *w, int P, double eta, int mask,
+                       double *coeffs /* n_cells * P * P * 2 */, int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+    nthreads_used = nthreads;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : err)
+#endif
+    for (int64_t j = 0; j < n_cells; ++j) {
+        oframe f;
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        int64_t o = offsets[j], Q = offsets[j + 1] - offsets[j];
+        if (type1_cell(&f, P, Q, x + o, y + o, h + o, w + o, coeffs + 2 * (size_t)P * P * j)) err |= 2;
+    }
+    return err ? -1 : 0;
+}
+
+int oracle_threads_used(void) { return nthreads_used; }
+
+/* ----------------------------------------------------------------------------------------- */
+/* Adjoint of the quadrature (type-2 sum): v_q = Re sum_mu G_mu e^{+i k_mu . x'_q}             */
+/* ----------------------------------------------------------------------------------------- */
+
+static double type2_point(const oframe *f, int P, const double *G, double xq, double yq) {
+    int half = P / 2;
+    double xp = (xq - f->cx) + f->H, yp = (yq - f->cy) + f->H;
+    double acc = 0.0;
+    for (int in = 0; in < P; ++in) {
+        double kn = 2.0 * ORACLE_PI * (double)(in - half) / f->L;
+        for (int im = 0; im < P; ++im) {
+            double km = 2.0 * ORACLE_PI * (double)(im - half) / f->L;
+            double ph = km * xp + kn * yp;
+            const double *g = G + 2 * ((size_t)in * P + im);
+            acc += g[0] * cos(ph) - g[1] * sin(ph);   /* Re(G e^{i ph}) */
+        }
+    }
+    return acc;
+}
+
+/* Exported: gradient of a real loss L(h, w) that depends on the coefficients only, given
+ * G = dL/dRe(h_mu) + i dL/dIm(h_mu) for every mode of every cell:
+ *   dL/dh_q = win_q w_q v_q / |D|,  dL/dw_q = win_q h_q v_q / |D|,  v_q = Re sum_mu G_mu e^{+i k.x'_q}. */
+int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
+                                const double *verts, const double *x, const double *y, const double *h,
+                                const double *w, int P, double eta, int mask, const double *G,
+                                double *grad_h, double *grad_w, int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : err)
+#endif
+    for (int64_t j = 0; j < n_cells; ++j) {
+        oframe f;
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        const double *Gj = G + 2 * (size_t)P * P * j;
+        for (int64_t q = offsets[j]; q < offsets[j + 1]; ++q) {
+            if (!in_window(&f, x[q], y[q])) {
+                grad_h[q] = 0.0;
+                grad_w[q] = 0.0;
+                continue;
+            }
+            double v = type2_point(&f, P, Gj, x[q], y[q]);
+            grad_h[q] = w[q] * v / f.area;
+            grad_w[q] = h[q] * v / f.area;
+        }
+    }
+    return err ? -1 : 0;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* Sec. 2.2: Elastic Mode Selection                                                            */
+/* ----------------------------------------------------------------------------------------- */
+
+typedef struct { double E; int32_t p; } epair;
+
+static int cmp_desc(const void *a, const void *b) {
+    const epair *x = (const epair *)a, *y = (const epair *)b;
+    if (x->E > y->E) return -1;
+    if (x->E < y->E) return 1;
+    return (x->p > y->p) - (x->p < y->p);   /* ties: ascending pair index */
+}
+
+/* Energy of the mode pair +-(m, n), Eq. "energy" generalised to pairs.  With fp32 != 0 the
+ * energy is formed in binary32 from binary32 coefficients with the fixed evaluation
+ * E = fma(re+, re+, im+ * im+) + fma(re-, re-, im- * im-), then times binary32(W); this is
+ * the precision the GPU takes this integer-deciding step in. */
+static double pair_energy(const double *c, int P, int m, int n, const double *W, int fp32, int dc) {
+    int half = P / 2;
+    size_t ip = (size_t)(n + half) * P + (m + half);
+    size_t in = (size_t)(-n + half) * P + (-m + half);
+    if (fp32) {
+        float rp = (float)c[2 * ip], ipp = (float)c[2 * ip + 1];
+        float rn = (float)c[2 * in], inn = (float)c[2 * in + 1];
+        float ep = fmaf(rp, rp, ipp * ipp);   /* compiled with -ffp-contract=off */
+        float en = fmaf(rn, rn, inn * inn);
+        float e = dc ? ep : ep + en;
+        if (W) e = e * (float)W[ip];
+        return (double)e;
+    }
+    double e = c[2 * ip] * c[2 * ip] + c[2 * ip + 1] * c[2 * ip + 1];
+    if (!dc) e += c[2 * in] * c[2 * in] + c[2 * in + 1] * c[2 * in + 1];
+    if (W) e *= W[ip];
+    return e;
+}
+
+typedef struct {
+    int k_min, k_max;
+    double alpha_min, alpha_max, delta, w1, w2;
+    int sum_all;      /* 0: HEAD reading (J_max), 1: ALL reading (J*) */
+    int include_dc;
+    int energy_fp32;
+} oems_params;
+
+/* Selection core on an unsorted list of J pair energies (Eqs. sorted_energy .. k_elastic).
+ * diag (optional, 10 doubles):
+ *   N_eff, S_delta, C, alpha_C, total, theta(K*), margin_rank, margin_theta, J*, n_positive */
+static void ems_select(epair *e, int J, const oems_params *pp, int32_t *kstar, int32_t *sel,
+                       double *retained, double *diag) {
+    qsort(e, J, sizeof(epair), cmp_desc);                       /* Eq. sorted_energy */
+    int Jmax = J < pp->k_max ? J : pp->k_max;                    /* footnote: J_max = min(J*, K_max) */
+    int nsum = pp->sum_all ? J : Jmax;
+    double M1 = 0.0, M2 = 0.0;
+    for (int j = 0; j < nsum; ++j) { M1 += e[j].E; M2 += e[j].E * e[j].E; }
+    int npos = 0;
+    for (int j = 0; j < J; ++j) npos += e[j].E > 0.0;
+    double neff = M2 > 0.0 ? M1 * M1 / M2 : 0.0;                 /* Eq. n_eff */
+    double S = 0.0;                                              /* Eq. s_delta */
+    if (Jmax >= 2) {
+        for (int j = 0; j < Jmax - 1; ++j)
+            if (e[j + 1].E > 0.0) S += exp(-(e[j].E / e[j + 1].E - 1.0) / pp->delta);
+        S /= (double)(Jmax - 1);
+    }
+    double nclip = neff < pp->k_max ? neff : (double)pp->k_max;
+    double C = pp->w1 * nclip / pp->k_max + pp->w2 * S;          /* Eq. c_score */
+    double alpha = pp->alpha_min + (pp->alpha_max - pp->alpha_min) * C;   /* Eq. alpha_c */
+    double total = M1;                                           /* denominator of Eq. f_cum */
+    int K = 0;
+    double cum = 0.0, theta_k = 0.0;
+    if (total > 0.0) {
+        int kthr = -1;
+        double cs = 0.0;
+        for (int j = 0; j < Jmax; ++j) {                         /* Eq. f_cum, Eq. k_elastic */
+            cs += e[j].E;
+            if (cs >= alpha * total) { kthr = j + 1; break; }
+        }
+        if (kthr < 0) kthr = pp->k_max;
+        K = kthr > pp->k_min ? kthr : pp->k_min;
+        if (K > pp->k_max) K = pp->k_max;
+        if (K > npos) K = npos;
+        if (K > J) K = J;
+        for (int j = 0; j < K; ++j) cum += e[j].E;
+        theta_k = cum / total;
+    }
+    *kstar = K;
+    for (int j = 0; j < pp->k_max; ++j) sel[j] = j < K ? e[j].p : -1;
+    *retained = cum;
+    if (diag) {
+        double mr = NAN, mt = NAN;
+        if (K > 0 && K < J && e[K - 1].E > 0.0) mr = (e[K - 1].E - e[K].E) / e[K - 1].E;
+        if (K > 0 && total > 0.0) {
+            double prev = (cum - e[K - 1].E) / total;
+            double a = theta_k - alpha, b = alpha - prev;
+            mt = a < b ? a : b;
+        }
+        diag[0] = neff; diag[1] = S; diag[2] = C; diag[3] = alpha; diag[4] = total;
+        diag[5] = theta_k; diag[6] = mr; diag[7] = mt; diag[8] = J; diag[9] = npos;
+    }
+}
+
+/* EMS on one P x P spectrum: pair energies of the symmetric box, then the selection core. */
+static int ems_cell(int P, const double *c, const double *W, const oems_params *pp, int32_t *kstar,
+                    int32_t *sel, double *retained, double *diag) {
+    int half = P / 2, lim = half - 1;
+    int cap = (2 * lim + 1) * (2 * lim + 1);
+    epair *e = (epair *)malloc(sizeof(epair) * (cap > 0 ? cap : 1));
+    if (!e) return -2;
+    int J = 0;
+    for (int n = -lim; n <= lim; ++n)
+        for (int m = -lim; m <= lim; ++m) {
+            int canon = (n > 0) || (n == 0 && m > 0);
+            int dc = (n == 0 && m == 0);
+            if (!(canon || (dc && pp->include_dc))) continue;
+            e[J].E = pair_energy(c, P, m, n, W, pp->energy_fp32, dc);
+            e[J].p = (n + half) * P + (m + half);
+            ++J;
+        }
+    ems_select(e, J, pp, kstar, sel, retained, diag);
+    free(e);
+    return 0;
+}
+
+/* Exported: EMS over a batch of spectra.  W: NULL, one P*P table shared by all cells
+ * (w_per_cell = 0), or one table per cell (w_per_cell = 1). */
+int oracle_ems_batch(int64_t n_cells, int P, const double *coeffs, const double *W, int w_per_cell,
+                     int k_min, int k_max, double alpha_min, double alpha_max, double delta, double w1,
+                     double w2, int sum_all, int include_dc, int energy_fp32, int32_t *kstar,
+                     int32_t *sel, double *retained, double *diag, int nthreads) {
+    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, include_dc, energy_fp32};
+    if (k_max < 1 || k_min < 0) return -1;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads) reduction(| : err)
+#endif
+    for (int64_t j = 0; j < n_cells; ++j) {
+        const double *Wj = W ? W + (w_per_cell ? (size_t)P * P * j : 0) : NULL;
+        if (ems_cell(P, coeffs + 2 * (size_t)P * P * j, Wj, &pp, kstar + j, sel + (size_t)k_max * j,
+                     retained + j, diag ? diag + 10 * j : NULL))
+            err |= 1;
+    }
+    return err ? -1 : 0;
+}
+
+/* Exported: EMS on an explicit list of J energies (any order), used to check the selection
+ * rules on the paper's spectral families; sel receives positions in the input list. */
+int oracle_ems_energies(int J, const double *E, int k_min, int k_max, double alpha_min, double alpha_max,
+                        double delta, double w1, double w2, int sum_all, int32_t *kstar, int32_t *sel,
+                        double *retained, double *diag) {
+    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, 0, 0};
+    if (k_max < 1 || k_min < 0) return -1;
+    epair *e = (epair *)malloc(sizeof(epair) * (J > 0 ? J : 1));
+    if (!e) return -2;
+    for (int j = 0; j < J; ++j) { e[j].E = E[j]; e[j].p = j; }
+    ems_select(e, J, &pp, kstar, sel, retained, diag);
+    free(e);
+    return 0;
+}
+
+/* Exported: G = grad_power_j * dP_j / d(coeffs) for the EMS-retained power
+ * P_j = sum_{p in S_j} W_p (|h_p|^2 + |h_-p|^2)  (S_j held fixed):  G_mu = 2 gp W_p h_mu on both
+ * members of every selected pair, 0 elsewhere. */
+int oracle_ems_grad_coeffs(int64_t n_cells, int P, const double *coeffs, const double *W, int w_per_cell,
+                           int k_max, const int32_t *kstar, const int32_t *sel, const double *grad_power,
+                           double *G) {
+    int half = P / 2;
+    memset(G, 0, sizeof(double) * 2 * (size_t)P * P * n_cells);
+    for (int64_t j = 0; j < n_cells; ++j) {
+        const double *c = coeffs + 2 * (size_t)P * P * j;
+        const double *Wj = W ? W + (w_per_cell ? (size_t)P * P * j : 0) : NULL;
+        double *g = G + 2 * (size_t)P * P * j;
+        for (int k = 0; k < kstar[j]; ++k) {
+            int p = sel[(size_t)k_max * j + k];
+            int m = p % P - half, n = p / P - half;
+            size_t ip = (size_t)p, in = (size_t)(-n + half) * P + (-m + half);
+            double wt = Wj ? Wj[ip] : 1.0;
+            double s = 2.0 * grad_power[j] * wt;
+            g[2 * ip] = s * c[2 * ip];
+            g[2 * ip + 1] = s * c[2 * ip + 1];
+            if (in != ip) {
+                g[2 * in] = s * c[2 * in];
+                g[2 * in + 1] = s * c[2 * in + 1];
+            }
+        }
+    }
+    return 0;
+}
