@@ -1,0 +1,191 @@
+/*
+ * enufft.h -- C ABI of the B300 (sm_103a) ENUFFT hot-path library.
+ *
+ * The library evaluates, for every cell of an unstructured triangular or hexagonal grid, the
+ * windowed quadrature sum of the paper "Elastic Non-Uniform FFT (ENUFFT)" (arxiv 2606.21278),
+ *
+ *     h_mn = 1/|D| sum_q win_q w_q h_q exp(-i (k_m x'_q + k_n y'_q)),   k_m = 2 pi m / L,
+ *
+ * (App. B, Eq. discrete_quadrature, with the local window of App. A), by a type-1 NUFFT
+ * (Sec. 2.1.2: spread, FFT, deconvolve) with an exponential-of-semicircle kernel, and then the
+ * Elastic Mode Selection of Sec. 2.2 on each spectrum.  It also provides the adjoint (type-2)
+ * needed for gradients of the EMS-retained power with respect to the samples and weights.
+ *
+ * Conventions shared by every call
+ *   - Pointers prefixed d_ are caller-owned DEVICE memory on the plan's device; nothing is
+ *     copied to or from the host during execution calls, and the library never frees them.
+ *   - Samples are grouped by cell in CSR form: cell j owns samples [offsets[j], offsets[j+1]).
+ *     x, y are local tangent-plane coordinates; h is elevation; w is the quadrature weight.
+ *     Arrays are plain SoA vectors of float (ENUFFT_FP32 / ENUFFT_MIXED plans) or double
+ *     (ENUFFT_FP64 plans).
+ *   - Coefficients are complex (interleaved re, im) float or double, laid out
+ *     coeffs[cell][n + P/2][m + P/2] for m, n in [-P/2, P/2) (row index n is the y mode).
+ *     They follow the paper's phase origin x' = u + H (App. A), so a cell's spectrum is
+ *     exactly the quadrature sum above.
+ *   - Every execution call is asynchronous and stream-ordered on the plan's stream; argument
+ *     errors are returned synchronously before anything is launched.  Conditions detected on
+ *     the device (non-finite coordinates, exhausted bounded waits) are latched in a device
+ *     status word and reported by enufft_sync_status().  The library never aborts or traps.
+ *   - A plan is bound to one device, one set of cells and one CSR offset vector; sample values
+ *     may change from call to call.  A plan is not thread-safe; distinct plans are.
+ */
+#ifndef ENUFFT_H
+#define ENUFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct enufft_plan_s *enufft_plan;
+
+typedef enum {
+    ENUFFT_OK = 0,
+    ENUFFT_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad option)       */
+    ENUFFT_ERR_CUDA = 2,         /* a CUDA runtime call failed                                   */
+    ENUFFT_ERR_NOMEM = 3,        /* device allocation failed                                     */
+    ENUFFT_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                           */
+    ENUFFT_ERR_UNSUPPORTED = 5,  /* option combination not implemented on this build             */
+    ENUFFT_ERR_DEVICE = 6        /* device-detected data error (e.g. non-finite coordinates)     */
+} enufft_status;
+
+typedef enum {
+    ENUFFT_FP64 = 0,   /* everything in binary64 (inputs/outputs double)                         */
+    ENUFFT_FP32 = 1,   /* plain binary32 per-cell launches (the comparison path)                 */
+    ENUFFT_MIXED = 2   /* product path: binary32 spreading/FFT with exact-binary32 coordinate
+                          transforms from binary64 per-cell constants, binary64 EMS sums          */
+} enufft_precision;
+
+typedef enum { ENUFFT_MASK_CELL = 0, ENUFFT_MASK_SQUARE = 1, ENUFFT_MASK_CIRCLE = 2 } enufft_mask;
+
+typedef struct {
+    int modes;            /* P, retained modes per dimension: even, 2..128                       */
+    double oversamp;      /* sigma >= 2: fine grid n_f = smallest power of two >= sigma * P      */
+    int kernel_width;     /* w (grid points) of the spreading kernel, 2..16                      */
+    double tol;           /* requested relative accuracy; w is raised to ceil(log10(1/tol)) + 1
+                             when that is larger (0 = use kernel_width as given)                  */
+    enufft_precision prec;
+    enufft_mask mask;     /* App. A support mask                                                 */
+    double eta;           /* App. A window expansion factor: H = (eta/2) * max extent            */
+    int tc_max_points;    /* cells with at most this many samples take the tensor-core direct
+                             sum (Eq. discrete_quadrature as a dense contraction); 0 = off       */
+} enufft_opts;
+
+typedef struct {
+    int k_min, k_max;                 /* spectral budget K_min <= K* <= K_max (Eq. k_elastic)     */
+    double alpha_min, alpha_max;      /* Eq. alpha_c                                              */
+    double delta;                     /* Eq. s_delta                                              */
+    double w1, w2;                    /* Eq. c_score                                              */
+    int sum_over;                     /* 0: sums over the top J_max = min(J*, K_max) energies
+                                         (footnote of Eq. alpha_c); 1: over all J* energies        */
+    int include_dc;                   /* 0: the (0,0) mode is not a candidate                     */
+} enufft_ems_params;
+
+/* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path. */
+void enufft_default_opts(enufft_opts *opts);
+/* Defaults of the paper's EMS illustration (Sec. 2.2): K_min 1, K_max 12, alpha 0..0.7,
+ * delta 0.02, w1 = w2 = 0.5, HEAD sums, DC excluded. */
+void enufft_default_ems(enufft_ems_params *params);
+
+/*
+ * Create a plan for n_cells cells (App. A window, Sec. 2.1.3 per-cell transforms).
+ *   d_cell_offsets  int64[n_cells + 1], non-decreasing, offsets[0] = 0 (device)
+ *   d_cell_nverts   int32[n_cells], convex polygon vertex counts in 3..6 (device)
+ *   d_cell_verts    double[n_cells][6][2] polygon vertices, either orientation (device)
+ *   cuda_stream     cudaStream_t for every call of this plan (NULL = legacy default stream)
+ * Computes the per-cell frames (centroid, H, L, |D|) on the device in binary64, copies the
+ * offsets to the host once to order cells by size and to route small cells, and allocates the
+ * plan's device state.  This call synchronises the stream.  On failure *out is NULL.
+ */
+enufft_status enufft_plan_create(enufft_plan *out, const enufft_opts *opts, int64_t n_cells,
+                                 const int64_t *d_cell_offsets, const int32_t *d_cell_nverts,
+                                 const double *d_cell_verts, void *cuda_stream);
+
+/* Release every resource of the plan (synchronises its stream first). NULL is accepted. */
+enufft_status enufft_plan_destroy(enufft_plan plan);
+
+/*
+ * Type-1 transform of every cell (Sec. 2.1.2 steps 1-4 with the App. A/B window and weights):
+ *   d_x, d_y, d_h, d_w  [N] samples (N = offsets[n_cells])
+ *   d_coeffs            [n_cells][P][P] complex output, every entry written
+ * Cells with no sample inside their window get all-zero coefficients.
+ */
+enufft_status enufft_type1(enufft_plan plan, const void *d_x, const void *d_y, const void *d_h,
+                           const void *d_w, void *d_coeffs);
+
+/*
+ * Elastic Mode Selection (Sec. 2.2, Eqs. energy .. k_elastic) on every cell's spectrum:
+ *   d_coeffs          [n_cells][P][P] complex (as written by enufft_type1)
+ *   d_mode_weights    NULL (all 1), double[P][P] shared by all cells (per_cell = 0) or
+ *                     double[n_cells][P][P] (per_cell = 1); a pair takes the weight of its
+ *                     half-plane member (Eq. weighted_e)
+ *   d_kstar           int32[n_cells]                  selected count K*
+ *   d_sel             int32[n_cells][k_max]           selected pair indices in decreasing energy,
+ *                     -1 padded; a pair +-(m,n) is named by its member with n > 0 or (n = 0,
+ *                     m > 0), encoded p = (n + P/2) * P + (m + P/2)
+ *   d_retained_power  double[n_cells]                 sum of the K* selected (weighted) energies
+ * Candidates are the pairs of the symmetric box |m|, |n| <= P/2 - 1.  Energies are formed in
+ * binary32 from binary32 coefficients (binary64 for FP64 plans); ranking ties go to the lower
+ * pair index; the cumulative power and its threshold test are binary64.
+ */
+enufft_status enufft_ems(enufft_plan plan, const void *d_coeffs, const double *d_mode_weights,
+                         int mode_weights_per_cell, const enufft_ems_params *params,
+                         int32_t *d_kstar, int32_t *d_sel, double *d_retained_power);
+
+/* enufft_type1 followed by enufft_ems, fused into one pass where the plan allows it (the
+ * spectrum is selected while it is still on chip).  Same arguments and results as the two calls. */
+enufft_status enufft_type1_ems(enufft_plan plan, const void *d_x, const void *d_y, const void *d_h,
+                               const void *d_w, void *d_coeffs, const double *d_mode_weights,
+                               int mode_weights_per_cell, const enufft_ems_params *params,
+                               int32_t *d_kstar, int32_t *d_sel, double *d_retained_power);
+
+/*
+ * Gradient of the EMS-retained power with the selection held fixed:
+ *   G_mu = 2 * grad_power[j] * W_p * h_mu on both members of each selected pair of cell j, 0 elsewhere,
+ * i.e. G = dL/dRe(h) + i dL/dIm(h) for L = sum_j grad_power[j] * retained_power[j].
+ *   d_coeffs, d_mode_weights, per_cell, d_kstar, d_sel as for enufft_ems (k_max from params)
+ *   d_grad_power      double[n_cells]
+ *   d_grad_coeffs     [n_cells][P][P] complex output (same precision as the coefficients)
+ */
+enufft_status enufft_ems_backward(enufft_plan plan, const void *d_coeffs, const double *d_mode_weights,
+                                  int mode_weights_per_cell, const enufft_ems_params *params,
+                                  const int32_t *d_kstar, const int32_t *d_sel,
+                                  const double *d_grad_power, void *d_grad_coeffs);
+
+/*
+ * Adjoint of enufft_type1 (a type-2 NUFFT: deconvolve, inverse FFT, interpolate):
+ *   d_grad_coeffs  [n_cells][P][P] complex G = dL/dRe(h_mn) + i dL/dIm(h_mn)
+ *   d_grad_h       [N] dL/dh_q = win_q w_q v_q / |D|     (may be NULL)
+ *   d_grad_w       [N] dL/dw_q = win_q h_q v_q / |D|     (may be NULL)
+ *   with v_q = Re sum_mn G_mn exp(+i (k_m x'_q + k_n y'_q)).
+ */
+enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs, const void *d_x,
+                                    const void *d_y, const void *d_h, const void *d_w, void *d_grad_h,
+                                    void *d_grad_w);
+
+/* Re-bind the plan to another stream of the same device (e.g. the caller's current stream);
+ * work already queued on the old stream is not waited for.  NULL selects the legacy default. */
+enufft_status enufft_set_stream(enufft_plan plan, void *cuda_stream);
+
+/* Synchronise the plan's stream and report (then clear) any latched device-side condition. */
+enufft_status enufft_sync_status(enufft_plan plan);
+
+/* Human-readable text of the last error on this plan (plan == NULL: of the calling thread). */
+const char *enufft_last_error(enufft_plan plan);
+
+/* Read-only plan facts: fine grid size, effective kernel width and shape parameter, and how many
+ * cells take each execution route.  Returns ENUFFT_ERR_ARG for a NULL plan or output. */
+typedef struct {
+    int modes, fine_grid, kernel_width;
+    double beta, oversamp_effective;
+    int64_t n_cells, n_points, cells_fused, cells_tensor, cells_large;
+    int precision;
+} enufft_plan_info;
+enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENUFFT_H */

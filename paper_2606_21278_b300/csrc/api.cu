@@ -1,0 +1,630 @@
+// api.cu -- host side of the C ABI declared in include/enufft.h.
+//
+// Plan creation does the per-plan constant work once: kernel width and shape (ES kernel,
+// exponential of semicircle), its piecewise polynomial for binary32 evaluation, the kernel's
+// Fourier transform Phi(k) for the deconvolution (Gauss-Legendre quadrature, binary64), the FFT
+// twiddles, the per-cell frames (device kernel, binary64) and the size-ordered work lists.
+// Execution calls only marshal arguments and launch kernels on the plan's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/enufft.h"
+#include "internal.h"
+#include "kernels_misc.cuh"
+
+using namespace enufft;
+
+namespace enufft {
+cudaError_t prepare_f32_64(int, int*, int*);
+cudaError_t prepare_f32_128(int, int*, int*);
+cudaError_t prepare_f64_64(int, int*, int*);
+cudaError_t prepare_f64_128(int, int*, int*);
+cudaError_t launch_fwd_f32_64(const FwdArgs<float>&, int, int, cudaStream_t);
+cudaError_t launch_fwd_f32_128(const FwdArgs<float>&, int, int, cudaStream_t);
+cudaError_t launch_fwd_f64_64(const FwdArgs<double>&, int, int, cudaStream_t);
+cudaError_t launch_fwd_f64_128(const FwdArgs<double>&, int, int, cudaStream_t);
+cudaError_t launch_adj_f32_64(const AdjArgs<float>&, int, int, cudaStream_t);
+cudaError_t launch_adj_f32_128(const AdjArgs<float>&, int, int, cudaStream_t);
+cudaError_t launch_adj_f64_64(const AdjArgs<double>&, int, int, cudaStream_t);
+cudaError_t launch_adj_f64_128(const AdjArgs<double>&, int, int, cudaStream_t);
+size_t smem_f32_64(int);
+size_t smem_f32_128(int);
+size_t smem_f64_64(int);
+size_t smem_f64_128(int);
+
+size_t fused_smem_bytes(bool dbl, int nf, int w) {
+    if (dbl) return nf == 64 ? smem_f64_64(w) : nf == 128 ? smem_f64_128(w) : 0;
+    return nf == 64 ? smem_f32_64(w) : nf == 128 ? smem_f32_128(w) : 0;
+}
+bool fused_supported(bool dbl, int nf, int w) {
+    const size_t b = fused_smem_bytes(dbl, nf, w);
+    return b > 0 && b <= 232448;
+}
+int fused_threads(int nf) { return nf >= 128 ? 512 : 256; }
+cudaError_t fused_prepare(bool dbl, int nf, int w, int* f, int* a) {
+    if (dbl) return nf == 64 ? prepare_f64_64(w, f, a) : prepare_f64_128(w, f, a);
+    return nf == 64 ? prepare_f32_64(w, f, a) : prepare_f32_128(w, f, a);
+}
+cudaError_t launch_type1(const FwdArgs<float>& a, int nf, int w, int grid, cudaStream_t s) {
+    return nf == 64 ? launch_fwd_f32_64(a, w, grid, s) : launch_fwd_f32_128(a, w, grid, s);
+}
+cudaError_t launch_type1(const FwdArgs<double>& a, int nf, int w, int grid, cudaStream_t s) {
+    return nf == 64 ? launch_fwd_f64_64(a, w, grid, s) : launch_fwd_f64_128(a, w, grid, s);
+}
+cudaError_t launch_adjoint(const AdjArgs<float>& a, int nf, int w, int grid, cudaStream_t s) {
+    return nf == 64 ? launch_adj_f32_64(a, w, grid, s) : launch_adj_f32_128(a, w, grid, s);
+}
+cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cudaStream_t s) {
+    return nf == 64 ? launch_adj_f64_64(a, w, grid, s) : launch_adj_f64_128(a, w, grid, s);
+}
+}  // namespace enufft
+
+// ------------------------------------------------------------------------------------------------
+// plan
+// ------------------------------------------------------------------------------------------------
+struct enufft_plan_s {
+    enufft_opts opts;
+    int P = 0, NF = 0, W = 0;
+    double beta = 0.0, sigma_eff = 0.0, poly_err = 0.0;
+    bool dbl = false;
+    int64_t n_cells = 0, n_points = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    CellConst* d_cells = nullptr;
+    int64_t* d_offsets = nullptr;
+    int* d_order = nullptr;          // all cells, largest first
+    int n_fused = 0;
+    unsigned* d_ctr = nullptr;       // [0] forward ticket, [1] adjoint ticket, [2] status
+    void* d_twiddle = nullptr;
+    int fwd_per_sm = 0, adj_per_sm = 0;
+    double inv_phi[kMaxHalf + 1] = {};
+    KernelPoly poly = {};
+    std::string err;
+};
+
+static thread_local std::string g_last_error;
+
+static enufft_status fail(enufft_plan p, enufft_status st, const std::string& msg) {
+    if (p)
+        p->err = msg;
+    else
+        g_last_error = msg;
+    return st;
+}
+static enufft_status cuda_fail(enufft_plan p, cudaError_t e, const char* where) {
+    return fail(p, e == cudaErrorMemoryAllocation ? ENUFFT_ERR_NOMEM : ENUFFT_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// exponential of semicircle kernel on z in [-1, 1]
+static double es_kernel(double z, double beta) {
+    if (std::fabs(z) > 1.0) return 0.0;
+    return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the Legendre recurrence)
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wts) {
+    x.resize(n);
+    wts.resize(n);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        wts[i] = wts[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Phi(k) = integral of phi(2 tau / W) e^{-2 pi i k tau / nf} d tau (grid units), the kernel's
+// Fourier transform used by the deconvolution (Sec. 2.1.2, Eq. deconv)
+static double kernel_ft(int k, int W, int nf, double beta, const std::vector<double>& x,
+                        const std::vector<double>& wts) {
+    const double pi = 3.14159265358979323846;
+    double s = 0.0;
+    for (size_t i = 0; i < x.size(); ++i) s += wts[i] * es_kernel(x[i], beta) * std::cos(pi * k * W * x[i] / nf);
+    return 0.5 * W * s;
+}
+
+// Piece i of the kernel as a function of t in [0, 1): phi((t - W/2 + i) 2 / W); fit on
+// u = 2t - 1 by Chebyshev interpolation with `deg` coefficients, returned as monomials in u.
+static double fit_pieces(int W, double beta, int deg, KernelPoly& kp) {
+    const double pi = 3.14159265358979323846;
+    kp.w = W;
+    kp.deg = deg;
+    kp.beta = (float)beta;
+    for (int i = 0; i < kMaxW; ++i)
+        for (int d = 0; d < kMaxDeg; ++d) kp.c[i][d] = 0.0f;
+    double maxerr = 0.0;
+    for (int i = 0; i < W; ++i) {
+        auto f = [&](double u) { return es_kernel(((u + 1.0) * 0.5 - 0.5 * W + i) * 2.0 / W, beta); };
+        std::vector<double> a(deg, 0.0), fk(deg);
+        for (int k = 0; k < deg; ++k) fk[k] = f(std::cos(pi * (k + 0.5) / deg));
+        for (int j = 0; j < deg; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < deg; ++k) s += fk[k] * std::cos(pi * j * (k + 0.5) / deg);
+            a[j] = (j == 0 ? 1.0 : 2.0) * s / deg;
+        }
+        // Chebyshev -> monomial: T_0 = 1, T_1 = u, T_{j+1} = 2 u T_j - T_{j-1}
+        std::vector<double> mono(deg, 0.0), tm1(deg, 0.0), t0(deg, 0.0), t1(deg, 0.0);
+        t0[0] = 1.0;
+        for (int j = 0; j < deg; ++j) {
+            const std::vector<double>& tj = (j == 0) ? t0 : t1;
+            for (int d = 0; d < deg; ++d) mono[d] += a[j] * tj[d];
+            std::vector<double> nx(deg, 0.0);
+            if (j == 0) {
+                if (deg > 1) nx[1] = 1.0;
+                tm1 = t0;
+                t1 = nx;
+            } else {
+                for (int d = 0; d + 1 < deg; ++d) nx[d + 1] += 2.0 * t1[d];
+                for (int d = 0; d < deg; ++d) nx[d] -= tm1[d];
+                tm1 = t1;
+                t1 = nx;
+            }
+        }
+        for (int d = 0; d < deg; ++d) kp.c[i][d] = (float)mono[d];
+        for (int s = 0; s <= 400; ++s) {
+            const double u = -1.0 + 2.0 * s / 400.0;
+            double v = 0.0;
+            for (int d = deg - 1; d >= 0; --d) v = v * u + mono[d];
+            maxerr = std::max(maxerr, std::fabs(v - f(u)));
+        }
+    }
+    return maxerr;
+}
+
+extern "C" {
+
+void enufft_default_opts(enufft_opts* o) {
+    if (!o) return;
+    o->modes = 64;
+    o->oversamp = 2.0;
+    o->kernel_width = 7;
+    o->tol = 0.0;
+    o->prec = ENUFFT_MIXED;
+    o->mask = ENUFFT_MASK_CELL;
+    o->eta = 1.5;
+    o->tc_max_points = 0;
+}
+
+void enufft_default_ems(enufft_ems_params* p) {
+    if (!p) return;
+    p->k_min = 1;
+    p->k_max = 12;
+    p->alpha_min = 0.0;
+    p->alpha_max = 0.7;
+    p->delta = 0.02;
+    p->w1 = 0.5;
+    p->w2 = 0.5;
+    p->sum_over = 0;
+    p->include_dc = 0;
+}
+
+const char* enufft_last_error(enufft_plan plan) { return plan ? plan->err.c_str() : g_last_error.c_str(); }
+
+enufft_status enufft_plan_destroy(enufft_plan p) {
+    if (!p) return ENUFFT_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->d_cells);
+    cudaFree(p->d_offsets);
+    cudaFree(p->d_order);
+    cudaFree(p->d_ctr);
+    cudaFree(p->d_twiddle);
+    cudaSetDevice(cur);
+    delete p;
+    return ENUFFT_OK;
+}
+
+enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int64_t n_cells,
+                                 const int64_t* d_cell_offsets, const int32_t* d_cell_nverts,
+                                 const double* d_cell_verts, void* cuda_stream) {
+    if (!out) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: out is NULL");
+    *out = nullptr;
+    if (!opts) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: opts is NULL");
+    if (n_cells < 0 || n_cells > (int64_t)0x7fffffff)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: n_cells out of range");
+    if (n_cells > 0 && (!d_cell_offsets || !d_cell_nverts || !d_cell_verts))
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: NULL cell array");
+    const enufft_opts& o = *opts;
+    if (o.modes < 2 || o.modes > 2 * kMaxHalf || (o.modes & 1))
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: modes must be even and in [2, 128]");
+    if (!(o.oversamp >= 2.0) || o.oversamp > 16.0)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: oversamp must be in [2, 16]");
+    if (o.kernel_width < 2 || o.kernel_width > kMaxW)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: kernel_width must be in [2, 16]");
+    if (o.prec != ENUFFT_FP64 && o.prec != ENUFFT_FP32 && o.prec != ENUFFT_MIXED)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad precision");
+    if (o.mask < 0 || o.mask > 2) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad mask");
+    if (!(o.eta > 0.0)) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: eta must be positive");
+    if (o.tol < 0.0 || o.tol >= 1.0) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: tol must be in [0, 1)");
+    if (o.tc_max_points < 0) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: tc_max_points < 0");
+
+    enufft_plan p = new enufft_plan_s();
+    p->opts = o;
+    p->P = o.modes;
+    p->dbl = o.prec == ENUFFT_FP64;
+    p->n_cells = n_cells;
+    p->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        enufft_status st = cuda_fail(nullptr, e, "cudaGetDevice");
+        delete p;
+        return st;
+    }
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+
+    // kernel width from the tolerance (ES kernel at sigma = 2: about one digit per grid point)
+    int W = o.kernel_width;
+    if (o.tol > 0.0) W = std::max(W, (int)std::ceil(std::log10(1.0 / o.tol)) + 1);
+    W = std::min(W, kMaxW);
+    // fine grid: smallest power of two >= sigma * P, at least 64
+    int NF = 64;
+    while (NF < o.oversamp * o.modes) NF *= 2;
+    p->W = W;
+    p->NF = NF;
+    p->sigma_eff = (double)NF / o.modes;
+    // ES shape: beta = 2.30 W at sigma = 2, scaled by (1 - 1/(2 sigma)) for other sigma
+    p->beta = 2.30 * W * (1.0 - 0.5 / p->sigma_eff) / 0.75;
+    if (o.prec == ENUFFT_FP32) {
+        enufft_plan_destroy(p);
+        return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the plain FP32 per-cell path is not built");
+    }
+    if (NF > 128 || !fused_supported(p->dbl, NF, W)) {
+        enufft_plan_destroy(p);
+        char buf[160];
+        snprintf(buf, sizeof buf, "plan_create: no kernel for %s n_f=%d width=%d", p->dbl ? "fp64" : "fp32", NF, W);
+        return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, buf);
+    }
+    if (!p->dbl) {
+        p->poly_err = fit_pieces(W, p->beta, std::min(W + 4, kMaxDeg), p->poly);
+    } else {
+        p->poly.w = W;
+        p->poly.beta = (float)p->beta;
+    }
+    {
+        std::vector<double> gx, gw;
+        gauss_legendre(256, gx, gw);
+        for (int k = 0; k <= p->P / 2; ++k) p->inv_phi[k] = 1.0 / kernel_ft(k, W, NF, p->beta, gx, gw);
+    }
+
+    // device state
+    const size_t tw_bytes = (size_t)NF * (p->dbl ? 16 : 8);
+    if ((e = cudaMalloc(&p->d_ctr, 4 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_twiddle, tw_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_cells, sizeof(CellConst) * std::max<int64_t>(n_cells, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_offsets, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_order, sizeof(int) * std::max<int64_t>(n_cells, 1))) != cudaSuccess) {
+        enufft_status st = cuda_fail(nullptr, e, "plan_create: cudaMalloc");
+        enufft_plan_destroy(p);
+        return st;
+    }
+    {
+        const double pi = 3.14159265358979323846;
+        if (p->dbl) {
+            std::vector<double> tw(2 * NF);
+            for (int j = 0; j < NF; ++j) { tw[2 * j] = std::cos(2 * pi * j / NF); tw[2 * j + 1] = -std::sin(2 * pi * j / NF); }
+            e = cudaMemcpyAsync(p->d_twiddle, tw.data(), tw_bytes, cudaMemcpyHostToDevice, p->stream);
+        } else {
+            std::vector<float> tw(2 * NF);
+            for (int j = 0; j < NF; ++j) {
+                tw[2 * j] = (float)std::cos(2 * pi * j / NF);
+                tw[2 * j + 1] = (float)-std::sin(2 * pi * j / NF);
+            }
+            e = cudaMemcpyAsync(p->d_twiddle, tw.data(), tw_bytes, cudaMemcpyHostToDevice, p->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    std::vector<int64_t> off(n_cells + 1, 0);
+    if (e == cudaSuccess && n_cells > 0) {
+        e = cudaMemcpyAsync(off.data(), d_cell_offsets, sizeof(int64_t) * (n_cells + 1), cudaMemcpyDeviceToHost,
+                            p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ctr, 0, 4 * sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) {
+        enufft_status st = cuda_fail(nullptr, e, "plan_create: copy");
+        enufft_plan_destroy(p);
+        return st;
+    }
+    if (off[0] != 0) {
+        enufft_plan_destroy(p);
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: offsets[0] must be 0");
+    }
+    for (int64_t j = 0; j < n_cells; ++j)
+        if (off[j + 1] < off[j]) {
+            enufft_plan_destroy(p);
+            return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: offsets must be non-decreasing");
+        }
+    p->n_points = off[n_cells];
+    // largest cells first (longest-processing-time order for the ticket queue); stable
+    std::vector<int> order(n_cells);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    p->n_fused = (int)n_cells;
+    if (n_cells > 0) {
+        e = cudaMemcpyAsync(p->d_order, order.data(), sizeof(int) * n_cells, cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_offsets, off.data(), sizeof(int64_t) * (n_cells + 1), cudaMemcpyHostToDevice,
+                                p->stream);
+        if (e == cudaSuccess) {
+            frame_kernel<<<(unsigned)((n_cells + 127) / 128), 128, 0, p->stream>>>(
+                n_cells, d_cell_nverts, d_cell_verts, o.eta, (int)o.mask, NF, p->d_cells);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) {
+            enufft_status st = cuda_fail(nullptr, e, "plan_create: frames");
+            enufft_plan_destroy(p);
+            return st;
+        }
+    } else {
+        cudaMemsetAsync(p->d_offsets, 0, sizeof(int64_t), p->stream);
+        cudaStreamSynchronize(p->stream);
+    }
+    e = fused_prepare(p->dbl, NF, W, &p->fwd_per_sm, &p->adj_per_sm);
+    if (e != cudaSuccess || p->fwd_per_sm < 1 || p->adj_per_sm < 1) {
+        enufft_status st = e != cudaSuccess ? cuda_fail(nullptr, e, "plan_create: kernel attributes")
+                                            : fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: kernel does not fit an SM");
+        enufft_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return ENUFFT_OK;
+}
+
+enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
+    if (!p || !info) return fail(p, ENUFFT_ERR_ARG, "get_plan_info: NULL argument");
+    info->modes = p->P;
+    info->fine_grid = p->NF;
+    info->kernel_width = p->W;
+    info->beta = p->beta;
+    info->oversamp_effective = p->sigma_eff;
+    info->n_cells = p->n_cells;
+    info->n_points = p->n_points;
+    info->cells_fused = p->n_fused;
+    info->cells_tensor = 0;
+    info->cells_large = 0;
+    info->precision = (int)p->opts.prec;
+    return ENUFFT_OK;
+}
+
+enufft_status enufft_set_stream(enufft_plan p, void* s) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "set_stream: NULL plan");
+    p->stream = (cudaStream_t)s;
+    return ENUFFT_OK;
+}
+
+enufft_status enufft_sync_status(enufft_plan p) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "sync_status: NULL plan");
+    unsigned st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, p->d_ctr + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "sync_status");
+    if (st) {
+        cudaMemsetAsync(p->d_ctr + 2, 0, sizeof(unsigned), p->stream);
+        cudaStreamSynchronize(p->stream);
+        std::string m = "device status:";
+        if (st & ST_NONFINITE) m += " non-finite sample(s) skipped;";
+        if (st & ST_BADCELL) m += " degenerate cell polygon(s);";
+        if (st & ST_TIMEOUT) m += " bounded wait expired;";
+        return fail(p, (st & ST_TIMEOUT) ? ENUFFT_ERR_TIMEOUT : ENUFFT_ERR_DEVICE, m);
+    }
+    return ENUFFT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// execution
+// ------------------------------------------------------------------------------------------------
+static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+static enufft_status check_ems_params(enufft_plan p, const enufft_ems_params* prm) {
+    if (!prm) return fail(p, ENUFFT_ERR_ARG, "ems: params is NULL");
+    if (prm->k_max < 1 || prm->k_max > kEmsMaxK) return fail(p, ENUFFT_ERR_ARG, "ems: k_max must be in [1, 64]");
+    if (prm->k_min < 0 || prm->k_min > prm->k_max) return fail(p, ENUFFT_ERR_ARG, "ems: k_min must be in [0, k_max]");
+    if (!(prm->delta > 0.0)) return fail(p, ENUFFT_ERR_ARG, "ems: delta must be positive");
+    return ENUFFT_OK;
+}
+
+static EmsArgs make_ems(const enufft_ems_params* prm, const double* W, int per_cell, int32_t* ks, int32_t* sel,
+                        double* ret) {
+    EmsArgs a;
+    a.k_min = prm->k_min;
+    a.k_max = prm->k_max;
+    a.alpha_min = prm->alpha_min;
+    a.alpha_max = prm->alpha_max;
+    a.delta = prm->delta;
+    a.w1 = prm->w1;
+    a.w2 = prm->w2;
+    a.sum_over = prm->sum_over ? 1 : 0;
+    a.include_dc = prm->include_dc ? 1 : 0;
+    a.W = W;
+    a.w_per_cell = per_cell ? 1 : 0;
+    a.kstar = ks;
+    a.sel = sel;
+    a.retained = ret;
+    return a;
+}
+
+template <typename T>
+static enufft_status run_type1(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
+                               void* coeffs, const EmsArgs* ems) {
+    FwdArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.x = (const T*)x;
+    a.y = (const T*)y;
+    a.h = (const T*)h;
+    a.w = (const T*)w;
+    a.coeffs = (T*)coeffs;
+    a.offsets = p->d_offsets;
+    a.cells = p->d_cells;
+    a.order = p->d_order;
+    a.n_work = p->n_fused;
+    a.P = p->P;
+    a.ticket = p->d_ctr + 0;
+    a.status = p->d_ctr + 2;
+    a.twiddle = (const cplx<T>*)p->d_twiddle;
+    for (int k = 0; k <= p->P / 2; ++k) a.inv_phi[k] = (T)p->inv_phi[k];
+    a.poly = p->poly;
+    a.beta = p->beta;
+    a.do_ems = ems ? 1 : 0;
+    if (ems) a.ems = *ems;
+    if (a.n_work == 0) return ENUFFT_OK;
+    cudaError_t e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "type1: memset");
+    const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_per_sm * p->num_sms);
+    e = launch_type1(a, p->NF, p->W, grid, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "type1: launch");
+    return ENUFFT_OK;
+}
+
+extern "C" {
+
+enufft_status enufft_type1(enufft_plan p, const void* d_x, const void* d_y, const void* d_h, const void* d_w,
+                           void* d_coeffs) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "type1: NULL plan");
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
+        return fail(p, ENUFFT_ERR_ARG, "type1: NULL data pointer");
+    if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1: coeffs must be 16-byte aligned");
+    cudaSetDevice(p->device);
+    return p->dbl ? run_type1<double>(p, d_x, d_y, d_h, d_w, d_coeffs, nullptr)
+                  : run_type1<float>(p, d_x, d_y, d_h, d_w, d_coeffs, nullptr);
+}
+
+enufft_status enufft_type1_ems(enufft_plan p, const void* d_x, const void* d_y, const void* d_h, const void* d_w,
+                               void* d_coeffs, const double* d_mode_weights, int per_cell,
+                               const enufft_ems_params* prm, int32_t* d_kstar, int32_t* d_sel,
+                               double* d_retained) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "type1_ems: NULL plan");
+    enufft_status st = check_ems_params(p, prm);
+    if (st != ENUFFT_OK) return st;
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || !d_kstar || !d_sel || !d_retained || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
+        return fail(p, ENUFFT_ERR_ARG, "type1_ems: NULL data pointer");
+    if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_ems: coeffs must be 16-byte aligned");
+    cudaSetDevice(p->device);
+    const EmsArgs ea = make_ems(prm, d_mode_weights, per_cell, d_kstar, d_sel, d_retained);
+    return p->dbl ? run_type1<double>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea)
+                  : run_type1<float>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea);
+}
+
+enufft_status enufft_ems(enufft_plan p, const void* d_coeffs, const double* d_mode_weights, int per_cell,
+                         const enufft_ems_params* prm, int32_t* d_kstar, int32_t* d_sel, double* d_retained) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "ems: NULL plan");
+    enufft_status st = check_ems_params(p, prm);
+    if (st != ENUFFT_OK) return st;
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || !d_kstar || !d_sel || !d_retained) return fail(p, ENUFFT_ERR_ARG, "ems: NULL data pointer");
+    cudaSetDevice(p->device);
+    const EmsArgs ea = make_ems(prm, d_mode_weights, per_cell, d_kstar, d_sel, d_retained);
+    const size_t smem = ems_smem_bytes(16, prm->k_max);
+    const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 4);
+    const int half = p->P / 2, lim = half - 1;
+    const int J = (lim > 0 ? lim * (2 * lim + 2) : 0) + 1;
+    const bool big = J > 16 * 32 * 4;
+    if (p->dbl) {
+        if (big) ems_kernel<double, 16><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea);
+        else ems_kernel<double, 4><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea);
+    } else {
+        if (big) ems_kernel<float, 16><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea);
+        else ems_kernel<float, 4><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: launch");
+}
+
+enufft_status enufft_ems_backward(enufft_plan p, const void* d_coeffs, const double* d_mode_weights, int per_cell,
+                                  const enufft_ems_params* prm, const int32_t* d_kstar, const int32_t* d_sel,
+                                  const double* d_grad_power, void* d_grad_coeffs) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "ems_backward: NULL plan");
+    enufft_status st = check_ems_params(p, prm);
+    if (st != ENUFFT_OK) return st;
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || !d_kstar || !d_sel || !d_grad_power || !d_grad_coeffs)
+        return fail(p, ENUFFT_ERR_ARG, "ems_backward: NULL data pointer");
+    if (!aligned16(d_grad_coeffs)) return fail(p, ENUFFT_ERR_ARG, "ems_backward: grad_coeffs must be 16-byte aligned");
+    cudaSetDevice(p->device);
+    const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 8);
+    if (p->dbl)
+        ems_backward_kernel<double><<<grid, 256, 0, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells,
+                                                               d_mode_weights, per_cell, prm->k_max, d_kstar, d_sel,
+                                                               d_grad_power, (cplx<double>*)d_grad_coeffs);
+    else
+        ems_backward_kernel<float><<<grid, 256, 0, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells,
+                                                              d_mode_weights, per_cell, prm->k_max, d_kstar, d_sel,
+                                                              d_grad_power, (cplx<float>*)d_grad_coeffs);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems_backward: launch");
+}
+
+}  // extern "C"
+
+template <typename T>
+static enufft_status run_adjoint(enufft_plan p, const void* g, const void* x, const void* y, const void* h,
+                                 const void* w, void* gh, void* gw) {
+    AdjArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.x = (const T*)x;
+    a.y = (const T*)y;
+    a.h = (const T*)h;
+    a.w = (const T*)w;
+    a.gcoef = (const T*)g;
+    a.grad_h = (T*)gh;
+    a.grad_w = (T*)gw;
+    a.offsets = p->d_offsets;
+    a.cells = p->d_cells;
+    a.order = p->d_order;
+    a.n_work = p->n_fused;
+    a.P = p->P;
+    a.ticket = p->d_ctr + 1;
+    a.status = p->d_ctr + 2;
+    a.twiddle = (const cplx<T>*)p->d_twiddle;
+    for (int k = 0; k <= p->P / 2; ++k) a.inv_phi[k] = (T)p->inv_phi[k];
+    a.poly = p->poly;
+    a.beta = p->beta;
+    if (a.n_work == 0) return ENUFFT_OK;
+    cudaError_t e = cudaMemsetAsync(p->d_ctr + 1, 0, sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "type1_backward: memset");
+    const int grid = std::min<int64_t>(a.n_work, (int64_t)p->adj_per_sm * p->num_sms);
+    e = launch_adjoint(a, p->NF, p->W, grid, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "type1_backward: launch");
+    return ENUFFT_OK;
+}
+
+extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad_coeffs, const void* d_x,
+                                               const void* d_y, const void* d_h, const void* d_w, void* d_grad_h,
+                                               void* d_grad_w) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "type1_backward: NULL plan");
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_grad_coeffs || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
+        return fail(p, ENUFFT_ERR_ARG, "type1_backward: NULL data pointer");
+    if (!aligned16(d_grad_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_backward: grad_coeffs must be 16-byte aligned");
+    cudaSetDevice(p->device);
+    return p->dbl ? run_adjoint<double>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w)
+                  : run_adjoint<float>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w);
+}

@@ -1,0 +1,71 @@
+// common.cuh -- device-side types shared by the ENUFFT kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace enufft {
+
+// --------------------------------------------------------------------------------------------
+// complex arithmetic (interleaved re, im; matches the C ABI coefficient layout)
+// --------------------------------------------------------------------------------------------
+template <typename T>
+struct cplx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.re * s, a.im * s}; }
+// multiply by -i
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul_mi(cplx<T> a) { return {a.im, -a.re}; }
+
+// --------------------------------------------------------------------------------------------
+// device status word (latched conditions, read by enufft_sync_status)
+// --------------------------------------------------------------------------------------------
+enum : unsigned {
+    ST_NONFINITE = 1u,   // a sample had a non-finite coordinate, elevation or weight (skipped)
+    ST_TIMEOUT = 2u,     // a bounded wait gave up
+    ST_BADCELL = 4u,     // a cell polygon was degenerate (zero area or bad vertex count)
+};
+
+// --------------------------------------------------------------------------------------------
+// per-cell constants, computed on the device by the frame kernel (App. A), binary64 first
+// --------------------------------------------------------------------------------------------
+struct CellConst {
+    // binary64 frame (App. A): centroid, half-width H, period L = 2H, |D|
+    double cx, cy, H, L, area;
+    double ux[6], uy[6];   // polygon vertices in the centred frame u = x - xbar (R = I)
+    double orient;         // +1 counter-clockwise, -1 clockwise
+    int nv, mask, valid, pad_;
+    // binary32 fast-path constants
+    float cxh, cxl, cyh, cyl;    // centroid as unevaluated binary32 sums hi + lo
+    float sch, scl;              // n_f / L as hi + lo
+    float inv_area;              // 1 / |D|
+    float Hf;                    // H rounded to binary32
+    float tau;                   // decision margin (length units) below which the binary64 test decides
+    float enx[6], eny[6], ed[6]; // outward unit edge normals and offsets: inside <=> n.u <= d
+    float pad2_[3];
+};
+
+// Spreading-kernel tables shared by the kernels of one plan (passed by value as a parameter).
+constexpr int kMaxW = 16;
+constexpr int kMaxDeg = 16;
+struct KernelPoly {
+    int w;            // kernel width (grid points)
+    int deg;          // number of monomial coefficients per piece
+    float beta;       // ES shape parameter
+    float c[kMaxW][kMaxDeg];   // piece i: phi_i(u) = sum_d c[i][d] u^d, u = 2 t - 1, t in [0, 1)
+};
+
+}  // namespace enufft

@@ -1,0 +1,24 @@
+// internal.h -- launch interface between the C-ABI host code and the kernel instantiations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "adjoint.cuh"
+#include "forward.cuh"
+
+namespace enufft {
+
+// Is (precision, n_f, W) compiled?  Shared-memory bytes and threads of the fused kernels.
+bool fused_supported(bool dbl, int nf, int w);
+size_t fused_smem_bytes(bool dbl, int nf, int w);
+int fused_threads(int nf);
+// Raise the dynamic shared-memory limit of both kernels of (precision, n_f, W) and return the
+// number of co-resident blocks per SM of the forward (fwd) and adjoint (adj) kernels.
+cudaError_t fused_prepare(bool dbl, int nf, int w, int* fwd_per_sm, int* adj_per_sm);
+
+cudaError_t launch_type1(const FwdArgs<float>& a, int nf, int w, int grid, cudaStream_t s);
+cudaError_t launch_type1(const FwdArgs<double>& a, int nf, int w, int grid, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjArgs<float>& a, int nf, int w, int grid, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cudaStream_t s);
+
+}  // namespace enufft

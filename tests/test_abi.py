@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI boundary: the library builds, loads, exports every symbol include/enufft.h
+declares, fills the documented defaults, and rejects bad arguments synchronously (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2606_21278_b300 as enufft
+from paper_2606_21278_b300 import build as enufft_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "enufft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    enufft_build.build()
+    return enufft.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(enufft_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for required in ("enufft_plan_create", "enufft_type1", "enufft_ems", "enufft_type1_backward",
+                     "enufft_plan_destroy", "enufft_type1_ems", "enufft_ems_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    out = subprocess.run(["nm", "-D", "--defined-only", enufft.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (enufft_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_build_targets_sm_103a_only():
+    assert enufft_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_defaults(lib):
+    o = enufft._Opts()
+    lib.enufft_default_opts(ctypes.byref(o))
+    assert (o.modes, o.oversamp, o.kernel_width, o.prec, o.mask, o.eta, o.tc_max_points) == (64, 2.0, 7, 2, 0, 1.5, 0)
+    e = enufft._Ems()
+    lib.enufft_default_ems(ctypes.byref(e))
+    assert (e.k_min, e.k_max, e.alpha_min, e.alpha_max, e.delta, e.w1, e.w2, e.sum_over, e.include_dc) == \
+        (1, 12, 0.0, 0.7, 0.02, 0.5, 0.5, 0, 0)
+
+
+@pytest.mark.parametrize("field,value", [("modes", 7), ("modes", 0), ("modes", 256), ("oversamp", 1.5),
+                                         ("kernel_width", 1), ("kernel_width", 17), ("prec", 9), ("mask", 5),
+                                         ("eta", 0.0), ("tol", -1.0), ("tc_max_points", -1)])
+def test_plan_create_rejects_bad_options(lib, field, value):
+    o = enufft._Opts()
+    lib.enufft_default_opts(ctypes.byref(o))
+    setattr(o, field, value)
+    h = ctypes.c_void_p(123)
+    st = lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), 0, None, None, None, None)
+    assert st == 1 and h.value is None
+    assert lib.enufft_last_error(None).decode().startswith("plan_create")
+
+
+def test_null_arguments_are_errors(lib):
+    h = ctypes.c_void_p()
+    assert lib.enufft_plan_create(ctypes.byref(h), None, 0, None, None, None, None) == 1
+    assert lib.enufft_plan_create(None, None, 0, None, None, None, None) == 1
+    o = enufft._Opts()
+    lib.enufft_default_opts(ctypes.byref(o))
+    assert lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), 4, None, None, None, None) == 1
+    assert lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), -1, None, None, None, None) == 1
+    for call, n in (("enufft_type1", 6), ("enufft_type1_backward", 8), ("enufft_sync_status", 1),
+                    ("enufft_set_stream", 2), ("enufft_get_plan_info", 2)):
+        assert getattr(lib, call)(*([None] * n)) == 1
+    e = enufft._Ems()
+    lib.enufft_default_ems(ctypes.byref(e))
+    assert lib.enufft_ems(None, None, None, 0, ctypes.byref(e), None, None, None) == 1
+    assert lib.enufft_plan_destroy(None) == 0
