@@ -15,7 +15,7 @@ import torch
 
 __all__ = ["Plan", "EMSParams", "EMSRetainedPower", "load_library", "LIB_PATH", "EnufftError"]
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libenufft.so")
+LIB_PATH = os.environ.get("ENUFFT_LIB", os.path.join(os.path.dirname(os.path.abspath(__file__)), "libenufft.so"))
 _lib = None
 
 _PREC = {"fp64": 0, "fp32": 1, "mixed": 2}

@@ -12,14 +12,14 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libenufft.so")
+BUILD = os.environ.get("ENUFFT_BUILD_DIR", os.path.join(HERE, "_build"))
+LIB = os.environ.get("ENUFFT_LIB", os.path.join(HERE, "libenufft.so"))
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", INCLUDE]
+         "-I", INCLUDE] + os.environ.get("ENUFFT_NVCC_FLAGS", "").split()
 
 
 def _deps() -> list[str]:

@@ -36,15 +36,6 @@ struct AdjArgs {
     double beta;
 };
 
-// two real rows as one complex row, read and written conjugated (inverse transform)
-template <typename T>
-struct RowPairConjAcc {
-    T* r0;
-    T* r1;
-    __device__ __forceinline__ cplx<T> load(int i) const { return {r0[i], -r1[i]}; }
-    __device__ __forceinline__ void store(int i, cplx<T> v) const { r0[i] = v.re; r1[i] = -v.im; }
-};
-
 template <int W, int GS, int J = 0, int I = 0>
 __device__ __forceinline__ float gather_taps(const float* __restrict__ g, const float (&kx)[W], const float (&ky)[W],
                                              float acc_row, float acc) {
@@ -70,10 +61,12 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
     cplx<T>* stw = reinterpret_cast<cplx<T>*>(smem + CF::grid_bytes + CF::c1_bytes);
     CellConst* scc = reinterpret_cast<CellConst*>(smem + CF::grid_bytes + CF::c1_bytes + CF::tw_bytes);
     int* sticket = reinterpret_cast<int*>(scc + 1);
+    T* sinv = reinterpret_cast<T*>(sticket + 4);
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int P = a.P, half = P / 2, C1S = half + 1;
     for (int i = tid; i < NF; i += CF::NT) stw[i] = a.twiddle[i];
+    for (int i = tid; i <= half; i += CF::NT) sinv[i] = a.inv_phi[i];
 
     for (;;) {
         if (tid == 0) *sticket = (int)atomicAdd(a.ticket, 1u);
@@ -83,9 +76,9 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
         const int cell = a.order[tk];
         cplx<T>* stage = reinterpret_cast<cplx<T>*>(sgrid);
         {   // per-cell constants; G of this cell into the staging area (coalesced 16-byte loads)
-            const int* src = reinterpret_cast<const int*>(a.cells + cell);
-            int* dst = reinterpret_cast<int*>(scc);
-            for (int i = tid; i < (int)(sizeof(CellConst) / 4); i += CF::NT) dst[i] = src[i];
+            const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
+            int4* dst = reinterpret_cast<int4*>(scc);
+            for (int i = tid; i < (int)(sizeof(CellConst) / 16); i += CF::NT) dst[i] = src[i];
             const float4* s4 = reinterpret_cast<const float4*>(a.gcoef + (size_t)cell * P * P * 2);
             float4* d4 = reinterpret_cast<float4*>(stage);
             const int n4 = P * P * (int)sizeof(cplx<T>) / 16;
@@ -104,7 +97,7 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                     f.re += g2.re;
                     f.im -= g2.im;
                 }
-                const T s = T(0.5) * a.inv_phi[m] * a.inv_phi[n < 0 ? -n : n];
+                const T s = T(0.5) * sinv[m] * sinv[n < 0 ? -n : n];
                 f.re *= s;
                 f.im *= s;
             }
@@ -115,7 +108,11 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
         {
             const int team = tid / N2, t = tid % N2;
             const unsigned tmask = ((1u << N2) - 1u) << (lane & ~(N2 - 1));
-            if (team <= half) team_fft<N1, N2, T>(StridedAcc<T, true>{sC1 + team, C1S}, t, stw, tmask);
+            if (team <= half) {   // workspace in the grid memory (the staged G is no longer needed)
+                cplx<T>* wk = reinterpret_cast<cplx<T>*>(sgrid) + (size_t)team * CF::WS_TEAM;
+                team_fft<N1, N2, T>(StridedAcc<T, true>{sC1 + team, C1S}, PlainAcc<T>{wk},
+                                    StridedAcc<T, true>{sC1 + team, C1S}, t, stw, tmask);
+            }
         }
         __syncthreads();
         // ---- 2b. rows in pairs: Z[m] = Y_m[y0] + i Y_m[y1] over m in [-P/2, P/2], inverse FFT
@@ -123,7 +120,7 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
             const int team = tid / N2, t = tid % N2;
             const unsigned tmask = ((1u << N2) - 1u) << (lane & ~(N2 - 1));
             if (team < NF / 2) {
-                T* r0 = sgrid + (HO + 2 * team) * GS + HO;
+                T* r0 = sgrid + (HO + 2 * team) * GS + HO;   // core columns of the row pair
                 T* r1 = r0 + GS;
                 const int y0 = 2 * team, y1 = y0 + 1;
                 for (int k = t; k < NF; k += N2) {
@@ -142,7 +139,8 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                     r1[k] = zi;
                 }
                 __syncwarp(tmask);
-                team_fft<N1, N2, T>(RowPairConjAcc<T>{r0, r1}, t, stw, tmask);
+                team_fft<N1, N2, T>(RowPairConjAcc<T>{r0, r1}, RowPairAcc<T>{r0 - HO, r1 - HO}, RowPairConjAcc<T>{r0, r1},
+                                    t, stw, tmask);
             }
         }
         __syncthreads();
@@ -164,6 +162,7 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
         // ---- 3+4. interpolate at the samples and scale
         if (scc->valid) {
             const CellConst& cc = *scc;
+            const FastFrame ff = fast_frame(cc);
             const int64_t q0 = a.offsets[cell], q1 = a.offsets[cell + 1];
             for (int64_t q = q0 + tid; q < q1; q += CF::NT) {
                 const T px = a.x[q], py = a.y[q], ph = a.h[q], pw = a.w[q];
@@ -172,7 +171,7 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                 bool in;
                 if constexpr (sizeof(T) == 4) {
                     float kx[W], ky[W];
-                    in = prep_f32<NF, W>(cc, a.poly, px, py, r0x, r0y, kx, ky, a.status);
+                    in = prep_f32<NF, W>(ff, cc.edge, cc, a.poly, px, py, r0x, r0y, kx, ky, a.status);
                     if (in) v = gather_taps<W, GS>(sgrid + (r0y + HO) * GS + (r0x + HO), kx, ky, 0.0f, 0.0f);
                 } else {
                     double kx[W], ky[W];
@@ -188,9 +187,9 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                 }
                 T gh = T(0), gw = T(0);
                 if (in) {
-                    if constexpr (sizeof(T) == 4) {
-                        gh = pw * v * cc.inv_area;
-                        gw = ph * v * cc.inv_area;
+                        if constexpr (sizeof(T) == 4) {
+                        gh = pw * v * ff.inv_area;
+                        gw = ph * v * ff.inv_area;
                     } else {
                         gh = pw * v / cc.area;
                         gw = ph * v / cc.area;

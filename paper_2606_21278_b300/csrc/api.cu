@@ -15,7 +15,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/enufft.h"
+#include "enufft.h"
 #include "internal.h"
 #include "kernels_misc.cuh"
 
@@ -82,6 +82,7 @@ struct enufft_plan_s {
     int* d_order = nullptr;          // all cells, largest first
     int n_fused = 0;
     unsigned* d_ctr = nullptr;       // [0] forward ticket, [1] adjoint ticket, [2] status
+    EmsScratch ems_scratch = {nullptr, nullptr};   // stage-1 EMS results per cell
     void* d_twiddle = nullptr;
     int fwd_per_sm = 0, adj_per_sm = 0;
     double inv_phi[kMaxHalf + 1] = {};
@@ -232,6 +233,8 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_order);
     cudaFree(p->d_ctr);
     cudaFree(p->d_twiddle);
+    cudaFree(p->ems_scratch.keys);
+    cudaFree(p->ems_scratch.info);
     cudaSetDevice(cur);
     delete p;
     return ENUFFT_OK;
@@ -298,7 +301,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, buf);
     }
     if (!p->dbl) {
-        p->poly_err = fit_pieces(W, p->beta, std::min(W + 4, kMaxDeg), p->poly);
+        p->poly_err = fit_pieces(W, p->beta, poly_deg(W), p->poly);
     } else {
         p->poly.w = W;
         p->poly.beta = (float)p->beta;
@@ -315,7 +318,9 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         (e = cudaMalloc(&p->d_twiddle, tw_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_cells, sizeof(CellConst) * std::max<int64_t>(n_cells, 1))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_offsets, sizeof(int64_t) * (n_cells + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&p->d_order, sizeof(int) * std::max<int64_t>(n_cells, 1))) != cudaSuccess) {
+        (e = cudaMalloc(&p->d_order, sizeof(int) * std::max<int64_t>(n_cells, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->ems_scratch.keys, sizeof(EmsKey) * kEmsMaxK * std::max<int64_t>(n_cells, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->ems_scratch.info, sizeof(EmsCellInfo) * std::max<int64_t>(n_cells, 1))) != cudaSuccess) {
         enufft_status st = cuda_fail(nullptr, e, "plan_create: cudaMalloc");
         enufft_plan_destroy(p);
         return st;
@@ -493,12 +498,18 @@ static enufft_status run_type1(enufft_plan p, const void* x, const void* y, cons
     a.beta = p->beta;
     a.do_ems = ems ? 1 : 0;
     if (ems) a.ems = *ems;
+    a.ems_out = p->ems_scratch;
     if (a.n_work == 0) return ENUFFT_OK;
     cudaError_t e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned), p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "type1: memset");
     const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_per_sm * p->num_sms);
     e = launch_type1(a, p->NF, p->W, grid, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "type1: launch");
+    if (ems) {
+        ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, *ems, p->ems_scratch);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1_ems: finish launch");
+    }
     return ENUFFT_OK;
 }
 
@@ -546,16 +557,20 @@ enufft_status enufft_ems(enufft_plan p, const void* d_coeffs, const double* d_mo
     const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 4);
     const int half = p->P / 2, lim = half - 1;
     const int J = (lim > 0 ? lim * (2 * lim + 2) : 0) + 1;
-    const bool big = J > 16 * 32 * 4;
+    const bool big = J > 512 * 4;   // candidates per thread of the 512-thread ranking block
+    const EmsScratch sc = p->ems_scratch;
     if (p->dbl) {
-        if (big) ems_kernel<double, 16><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea);
-        else ems_kernel<double, 4><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea);
+        if (big) ems_rank_kernel<double, 16><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
+        else ems_rank_kernel<double, 4><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
     } else {
-        if (big) ems_kernel<float, 16><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea);
-        else ems_kernel<float, 4><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea);
+        if (big) ems_rank_kernel<float, 16><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
+        else ems_rank_kernel<float, 4><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
     }
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: launch");
+    if (e != cudaSuccess) return cuda_fail(p, e, "ems: launch");
+    ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, ea, sc);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: finish launch");
 }
 
 enufft_status enufft_ems_backward(enufft_plan p, const void* d_coeffs, const double* d_mode_weights, int per_cell,

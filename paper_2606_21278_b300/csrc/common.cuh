@@ -54,13 +54,25 @@ struct CellConst {
     float inv_area;              // 1 / |D|
     float Hf;                    // H rounded to binary32
     float tau;                   // decision margin (length units) below which the binary64 test decides
-    float enx[6], eny[6], ed[6]; // outward unit edge normals and offsets: inside <=> n.u <= d
     float pad2_[3];
+    float4 edge[6];              // outward unit edge normal (x, y) and offset z: inside <=> n.u <= z
 };
+
+// binary32 frame constants of the current cell, held in registers by every thread
+struct FastFrame {
+    float cxh, cxl, cyh, cyl, sch, scl, inv_area, Hf, tau;
+    int mask, nv;
+};
+
+__device__ __forceinline__ FastFrame fast_frame(const CellConst& cc) {
+    return FastFrame{cc.cxh, cc.cxl, cc.cyh, cc.cyl, cc.sch, cc.scl, cc.inv_area, cc.Hf, cc.tau, cc.mask, cc.nv};
+}
 
 // Spreading-kernel tables shared by the kernels of one plan (passed by value as a parameter).
 constexpr int kMaxW = 16;
 constexpr int kMaxDeg = 16;
+// monomial coefficients per kernel piece used for width W (binary32 Horner evaluation)
+__host__ __device__ constexpr int poly_deg(int W) { return W + 4 < kMaxDeg ? W + 4 : kMaxDeg; }
 struct KernelPoly {
     int w;            // kernel width (grid points)
     int deg;          // number of monomial coefficients per piece

@@ -1,16 +1,25 @@
-// ems.cuh -- Elastic Mode Selection of one spectrum by one thread block (Sec. 2.2).
+// ems.cuh -- Elastic Mode Selection (Sec. 2.2) in two stages.
 //
 // Candidates are the mode pairs +-(m, n) of the symmetric box |m|, |n| <= P/2 - 1, named by the
-// half-plane member (n > 0, or n == 0 and m > 0), p = (n + P/2) P + (m + P/2).  The block
-//   1. forms every pair energy E_p = |h_p|^2 + |h_-p|^2 (times W_p), Eqs. energy / weighted_e,
-//      with one fixed evaluation order so that reruns are bitwise identical;
-//   2. selects the K_max largest by a segmented tournament: each warp ranks its own segment
-//      (per-lane sorted registers, warp-wide argmax rounds), then one warp merges the sorted
-//      warp lists (Eq. sorted_energy; ties go to the lower pair index);
-//   3. evaluates N_eff, S_delta, C, alpha_C and the cumulative fraction theta(K) in binary64 and
-//      thresholds it (Eqs. n_eff, s_delta, c_score, alpha_c, f_cum, k_elastic), in the same
-//      operation order as the definition so that equal energies give equal decisions.
+// half-plane member (n > 0, or n == 0 and m > 0), p = (n + P/2) P + (m + P/2).
+//
+// Stage 1, ranking (one thread block per spectrum, inside the fused transform kernel or the
+// standalone EMS kernel):
+//   - every pair energy E_p = |h_p|^2 + |h_-p|^2 (times W_p), Eqs. energy / weighted_e, formed in
+//     one fixed evaluation order so that reruns are bitwise identical;
+//   - the K_max largest (Eq. sorted_energy; ties go to the lower pair index) by a radix select on
+//     the energy bits followed by a small ordering of the survivors;
+//   - the number of positive energies and, for the ALL reading only, sum E and sum E^2 over all
+//     pairs as unevaluated binary32 pairs (error-free transformations, ~48-bit accurate);
+//   written to per-cell scratch.
+// Stage 2, the elastic count (one thread per cell, binary64): N_eff, S_delta, C, alpha_C, the
+// cumulative fraction theta(K) and K* (Eqs. n_eff, s_delta, c_score, alpha_c, f_cum, k_elastic),
+// in the definition's operation order so that equal energies give equal decisions.  Doing this
+// scalar binary64 work one cell per lane keeps B300's narrow binary64 pipe fully occupied instead
+// of stalling a whole thread block on one lane.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -38,17 +47,39 @@ struct EmsKey {
     unsigned int pad_;
 };
 
+// per-cell result of stage 1
+struct EmsCellInfo {
+    int L;          // keys found (<= K_max)
+    int J;          // candidate pairs J*
+    int npos;       // pairs with positive energy
+    int is_f64;     // energies are binary64 bits (else binary32 bits)
+    float m1h, m1l, m2h, m2l;   // ALL reading: sum E and sum E^2 as hi + lo
+    double m1d, m2d;            // ALL reading, binary64 energies
+};
+
+struct EmsScratch {
+    EmsKey* keys;        // [n_cells][kEmsMaxK]
+    EmsCellInfo* info;   // [n_cells]
+};
+
 __device__ __forceinline__ bool key_better(const EmsKey& a, const EmsKey& b) {
     return a.e > b.e || (a.e == b.e && a.q > b.q);
 }
-__device__ __forceinline__ EmsKey key_shfl_xor(const EmsKey& k, int m) {
-    EmsKey r;
-    r.e = __shfl_xor_sync(0xffffffffu, k.e, m);
-    r.q = __shfl_xor_sync(0xffffffffu, k.q, m);
-    r.pad_ = 0;
-    return r;
+
+// error-free binary32 sum (Knuth TwoSum) and product (FMA)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-__device__ __forceinline__ bool key_is_pad(const EmsKey& k) { return k.e == 0ull && k.q == 0u; }
+// (ah + al) + (bh + bl) as a renormalised pair
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+    float s, e;
+    two_sum_f(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    ah = __fadd_rn(s, e);
+    al = __fsub_rn(e, __fsub_rn(ah, s));
+}
 
 // energy of the pair (m, n) in the kernel's fixed order; T = float -> binary32, double -> binary64
 template <typename T>
@@ -63,7 +94,6 @@ struct EnergyOf<float> {
         return e;
     }
     static __device__ __forceinline__ unsigned long long bits(float e) { return (unsigned long long)__float_as_uint(e); }
-    static __device__ __forceinline__ double value(unsigned long long b) { return (double)__uint_as_float((unsigned)b); }
 };
 template <>
 struct EnergyOf<double> {
@@ -74,186 +104,295 @@ struct EnergyOf<double> {
         return e;
     }
     static __device__ __forceinline__ unsigned long long bits(double e) { return (unsigned long long)__double_as_longlong(e); }
-    static __device__ __forceinline__ double value(unsigned long long b) { return __longlong_as_double((long long)b); }
 };
 
-// shared-memory scratch of the block EMS: nwarps * k_max list keys + k_max merged keys + reductions
-__host__ __device__ constexpr size_t ems_smem_bytes(int nwarps, int k_max) {
-    return sizeof(EmsKey) * (size_t)(nwarps + 1) * k_max + sizeof(double) * 2 * nwarps + sizeof(int) * nwarps + 64;
+__device__ __forceinline__ double key_value(const EmsKey& k, int is_f64) {
+    return is_f64 ? __longlong_as_double((long long)k.e) : (double)__uint_as_float((unsigned)k.e);
 }
 
-// Block-wide EMS of one spectrum.  Spec provides get(m, n) -> cplx<T> for m, n in [-P/2, P/2).
-// R: upper bound of candidates per lane per warp segment (compile time).  All threads of the
-// block must call it; it ends with a __syncthreads().
-template <typename T, int R, typename Spec>
-__device__ void ems_block(const Spec& spec, int P, int cell, const EmsArgs& a, unsigned char* smem) {
-    using EN = EnergyOf<T>;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int half = P / 2, lim = half - 1, row = 2 * lim + 1;
-    const int J = (lim > 0 ? lim + lim * row : 0) + (a.include_dc ? 1 : 0);
-    const int K = a.k_max;
-    EmsKey* lists = reinterpret_cast<EmsKey*>(smem);
-    EmsKey* top = lists + (size_t)nwarps * K;
-    double* red = reinterpret_cast<double*>(top + K);
-    int* cnt = reinterpret_cast<int*>(red + 2 * nwarps);
-    const double* Wc = a.W ? a.W + (a.w_per_cell ? (size_t)cell * P * P : 0) : nullptr;
+// shared-memory scratch of stage 1: digit histogram, selected keys, reductions
+__host__ __device__ constexpr size_t ems_smem_bytes(int nwarps, int k_max) {
+    return sizeof(unsigned) * 256 + sizeof(EmsKey) * (size_t)k_max + sizeof(float) * 4 * nwarps +
+           sizeof(double) * 2 * nwarps + sizeof(int) * (2 * nwarps + 8) + 64;
+}
 
-    // ---- 1. energies of this warp's segment (register-major: slot r of lane l = r * 32 + l)
-    const int seg = (J + nwarps - 1) / nwarps;
-    const int s0 = warp * seg, s1 = min(J, s0 + seg);
-    EmsKey key[R];
-    double m1 = 0.0, m2 = 0.0;
+// candidate j (0 .. J-1) -> mode (m, n); with the DC mode first when it is a candidate, the pair
+// index p = (n + P/2) P + (m + P/2) increases with j, so "lower index first" is "lower j first"
+__device__ __forceinline__ void ems_mode_of(int j, int lim, int row, int dc_first, int& m, int& n) {
+    if (dc_first) {
+        if (j == 0) { m = 0; n = 0; return; }
+        --j;
+    }
+    if (j < lim) {
+        m = j + 1;
+        n = 0;
+    } else {
+        const int jj = j - lim;
+        n = 1 + jj / row;
+        m = jj % row - lim;
+    }
+}
+
+// Stage 1 for one spectrum by the whole block.  Spec provides get(m, n) -> cplx<T> for
+// m, n in [-P/2, P/2).  R: upper bound of candidates per thread (compile time).  All threads of
+// the block must call it; it ends with a __syncthreads().
+//
+// The K_max largest energies are found by a most-significant-digit radix select on the energy
+// bits (8-bit digits, one shared-memory histogram pass per digit), which yields the K-th largest
+// value T; the keys above T are kept, and of the keys equal to T those with the lowest pair
+// index, found by a block prefix count in candidate order.  One warp then orders the <= K_max
+// survivors by (energy desc, index asc).
+template <typename T, int R, typename Spec>
+__device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs& a, const EmsScratch& out,
+                               unsigned char* smem) {
+    using EN = EnergyOf<T>;
+    using U = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+    constexpr int NDIG = (int)sizeof(U);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarps = nt >> 5;
+    const int half = P / 2, lim = half - 1, row = 2 * lim + 1;
+    const int dc = a.include_dc ? 1 : 0;
+    const int J = (lim > 0 ? lim + lim * row : 0) + dc;
+    const int K = a.k_max;
+    unsigned* hist = reinterpret_cast<unsigned*>(smem);
+    EmsKey* keep = reinterpret_cast<EmsKey*>(hist + 256);
+    float* redf = reinterpret_cast<float*>(keep + K);
+    double* redd = reinterpret_cast<double*>(redf + 4 * nwarps);
+    int* wsum = reinterpret_cast<int*>(redd + 2 * nwarps);     // [nwarps] warp totals
+    int* ctl = wsum + 2 * nwarps;                             // [0] prefix lo, [1] prefix hi, [2] remaining, [3] kept
+    const double* Wc = a.W ? a.W + (a.w_per_cell ? (size_t)cell * P * P : 0) : nullptr;
+    const bool all = a.sum_over != 0;
+
+    // ---- energies, candidates j = tid * R + r (contiguous per thread)
+    U u[R];
+    float m1h = 0.f, m1l = 0.f, m2h = 0.f, m2l = 0.f;
+    double m1d = 0.0, m2d = 0.0;
     int npos = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int j = s0 + r * 32 + lane;
-        key[r] = EmsKey{0ull, 0u, 0u};
-        if (j < s1) {
+        const int j = tid * R + r;
+        u[r] = 0;
+        if (j < J) {
             int m, n;
-            bool dc = false;
-            if (a.include_dc && j == J - 1) {
-                m = 0; n = 0; dc = true;
-            } else if (j < lim) {
-                m = j + 1; n = 0;
-            } else {
-                const int jj = j - lim;
-                n = 1 + jj / row;
-                m = jj % row - lim;
-            }
+            ems_mode_of(j, lim, row, dc, m, n);
+            const bool isdc = (m == 0 && n == 0);
             const int p = (n + half) * P + (m + half);
-            const T e = EN::pair(spec.get(m, n), spec.get(-m, -n), dc, Wc ? Wc[p] : 1.0, Wc != nullptr);
-            key[r] = EmsKey{EN::bits(e), ~(unsigned)p, 0u};
-            const double ed = (double)e;
-            m1 += ed;
-            m2 += ed * ed;
-            npos += ed > 0.0;
-        }
-    }
-    // per-lane descending order of the R slots (small sorting network)
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-        for (int k = R - 1; k > i; --k)
-            if (key_better(key[k], key[k - 1])) {
-                EmsKey t = key[k]; key[k] = key[k - 1]; key[k - 1] = t;
+            const T e = EN::pair(spec.get(m, n), spec.get(-m, -n), isdc, Wc ? Wc[p] : 1.0, Wc != nullptr);
+            u[r] = (U)EN::bits(e);
+            npos += e > T(0);
+            if (all) {
+                if constexpr (sizeof(T) == 4) {
+                    const float sq = __fmul_rn(e, e), sqe = __fmaf_rn(e, e, -sq);
+                    df_add(m1h, m1l, e, 0.f);
+                    df_add(m2h, m2l, sq, sqe);
+                } else {
+                    m1d += e;
+                    m2d += e * e;
+                }
             }
-    // ---- 2a. warp tournament: K rounds of a 32-way argmax over the lanes' heads
-    int got = 0;
-    for (int k = 0; k < K; ++k) {
-        EmsKey best = key[0];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            EmsKey other = key_shfl_xor(best, o);
-            if (key_better(other, best)) best = other;
         }
-        if (key_is_pad(best)) break;
-        const bool mine = (key[0].e == best.e && key[0].q == best.q);
-        if (mine) {
+    }
+    const int Kt = K < J ? K : J;   // keys to keep
+    // ---- radix select of the Kt-th largest energy (digits from the most significant)
+    U prefix = 0, pmask = 0;
+    int remaining = Kt;
+    for (int d = NDIG - 1; d >= 0 && Kt > 0; --d) {
+        const int shift = 8 * d;
+        for (int i = tid; i < 256; i += nt) hist[i] = 0;
+        __syncthreads();
 #pragma unroll
-            for (int r = 0; r < R - 1; ++r) key[r] = key[r + 1];
-            key[R - 1] = EmsKey{0ull, 0u, 0u};
+        for (int r = 0; r < R; ++r) {
+            const int j = tid * R + r;
+            if (j < J && (u[r] & pmask) == prefix) atomicAdd(&hist[(unsigned)(u[r] >> shift) & 255u], 1u);
         }
-        if (lane == 0) lists[(size_t)warp * K + k] = best;
-        ++got;
-    }
-    // reductions for the ALL reading and for the positive count
+        __syncthreads();
+        if (warp == 0) {
+            // lane l owns digits 255 - 8l .. 248 - 8l (descending); exclusive scan from the top
+            unsigned c8[8], tot = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-        npos += __shfl_xor_sync(0xffffffffu, npos, o);
+            for (int k = 0; k < 8; ++k) { c8[k] = hist[255 - 8 * lane - k]; tot += c8[k]; }
+            unsigned incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            unsigned before = incl - tot;   // keys with a larger digit than this lane's first digit
+            int found = -1;
+            unsigned above = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (found < 0 && before + c8[k] >= (unsigned)remaining && before < (unsigned)remaining) {
+                    found = 255 - 8 * lane - k;
+                    above = before;
+                }
+                before += c8[k];
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, found >= 0);
+            const int src = __ffs(ball) - 1;
+            const int dig = __shfl_sync(0xffffffffu, found, src);
+            const unsigned ab = __shfl_sync(0xffffffffu, above, src);
+            if (lane == 0) {
+                ctl[0] = dig;
+                ctl[2] = remaining - (int)ab;
+            }
+        }
+        __syncthreads();
+        prefix |= (U)ctl[0] << shift;
+        pmask |= (U)255 << shift;
+        remaining = ctl[2];
+        __syncthreads();
     }
-    if (lane == 0) {
-        red[2 * warp] = m1;
-        red[2 * warp + 1] = m2;
-        cnt[warp] = got | (npos << 8);
+    // ---- keep the keys above the threshold and the first `remaining` keys equal to it
+    if (tid == 0) ctl[3] = 0;
+    int eq = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) eq += (tid * R + r < J && u[r] == prefix && Kt > 0);
+    int incl = eq;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    // ---- 2b. merge of the sorted warp lists by warp 0, then the scalar EMS by lane 0
-    if (warp == 0) {
-        int len = 0, pos = 0;
-        EmsKey head{0ull, 0u, 0u};
-        if (lane < nwarps) {
-            len = cnt[lane] & 0xff;
-            if (len > 0) head = lists[(size_t)lane * K];
+    int rank = incl - eq;   // equal keys before this thread, in candidate order
+    for (int w = 0; w < warp; ++w) rank += wsum[w];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = tid * R + r;
+        if (j < J && Kt > 0) {
+            bool take = u[r] > prefix;
+            if (u[r] == prefix) take = rank++ < remaining;
+            if (take) {
+                int m, n;
+                ems_mode_of(j, lim, row, dc, m, n);
+                const int slot = atomicAdd(&ctl[3], 1);
+                keep[slot] = EmsKey{(unsigned long long)u[r], ~(unsigned)((n + half) * P + (m + half)), 0u};
+            }
         }
-        int L = 0;
-        for (int k = 0; k < K; ++k) {
-            EmsKey best = head;
+    }
+    // ---- reductions (positive count; ALL-reading sums)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npos += __shfl_xor_sync(0xffffffffu, npos, o);
+    if (all) {
+        if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                EmsKey other = key_shfl_xor(best, o);
-                if (key_better(other, best)) best = other;
+                const float a1 = __shfl_xor_sync(0xffffffffu, m1h, o), b1 = __shfl_xor_sync(0xffffffffu, m1l, o);
+                const float a2 = __shfl_xor_sync(0xffffffffu, m2h, o), b2 = __shfl_xor_sync(0xffffffffu, m2l, o);
+                df_add(m1h, m1l, a1, b1);
+                df_add(m2h, m2l, a2, b2);
             }
-            if (key_is_pad(best)) break;
-            if (lane < nwarps && head.e == best.e && head.q == best.q) {
-                ++pos;
-                head = pos < len ? lists[(size_t)lane * K + pos] : EmsKey{0ull, 0u, 0u};
+        } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                m1d += __shfl_xor_sync(0xffffffffu, m1d, o);
+                m2d += __shfl_xor_sync(0xffffffffu, m2d, o);
             }
-            if (lane == 0) top[k] = best;
-            ++L;
         }
-        __syncwarp();
-        if (lane == 0) {
-            int npos_all = 0;
-            double A1 = 0.0, A2 = 0.0;
-            for (int w = 0; w < nwarps; ++w) {
-                npos_all += cnt[w] >> 8;
-                A1 += red[2 * w];
-                A2 += red[2 * w + 1];
-            }
-            const int Jmax = J < K ? J : K;
-            double M1 = 0.0, M2 = 0.0;
-            if (a.sum_over) {
-                M1 = A1;
-                M2 = A2;
-            } else {
-                for (int j = 0; j < Jmax; ++j) {
-                    const double e = EN::value(top[j].e);
-                    M1 = __dadd_rn(M1, e);
-                    M2 = __dadd_rn(M2, __dmul_rn(e, e));
-                }
-            }
-            const double neff = M2 > 0.0 ? __ddiv_rn(__dmul_rn(M1, M1), M2) : 0.0;
-            double S = 0.0;
-            if (Jmax >= 2) {
-                for (int j = 0; j < Jmax - 1; ++j) {
-                    const double e0 = EN::value(top[j].e), e1 = EN::value(top[j + 1].e);
-                    if (e1 > 0.0) S = __dadd_rn(S, exp(__ddiv_rn(-__dsub_rn(__ddiv_rn(e0, e1), 1.0), a.delta)));
-                }
-                S = __ddiv_rn(S, (double)(Jmax - 1));
-            }
-            const double nclip = neff < (double)K ? neff : (double)K;
-            const double C = __dadd_rn(__ddiv_rn(__dmul_rn(a.w1, nclip), (double)K), __dmul_rn(a.w2, S));
-            const double alpha = __dadd_rn(a.alpha_min, __dmul_rn(__dsub_rn(a.alpha_max, a.alpha_min), C));
-            const double total = M1;
-            int Ks = 0;
-            double cum = 0.0;
-            if (total > 0.0) {
-                int kthr = -1;
-                double cs = 0.0;
-                for (int j = 0; j < Jmax; ++j) {
-                    cs = __dadd_rn(cs, EN::value(top[j].e));
-                    if (cs >= __dmul_rn(alpha, total)) { kthr = j + 1; break; }
-                }
-                if (kthr < 0) kthr = K;
-                Ks = kthr > a.k_min ? kthr : a.k_min;
-                if (Ks > K) Ks = K;
-                if (Ks > npos_all) Ks = npos_all;
-                if (Ks > J) Ks = J;
-                if (Ks > L) Ks = L;
-                for (int j = 0; j < Ks; ++j) cum = __dadd_rn(cum, EN::value(top[j].e));
-            }
-            a.kstar[cell] = Ks;
-            a.retained[cell] = cum;
-            cnt[0] = Ks;
-        }
-        __syncwarp();
-        const int Ks = cnt[0];
-        for (int k = lane; k < K; k += 32)
-            a.sel[(size_t)cell * K + k] = k < Ks ? (int)(~top[k].q) : -1;
+    }
+    __syncthreads();   // keep[] complete, wsum reads done
+    if (lane == 0) {
+        redf[4 * warp + 0] = m1h; redf[4 * warp + 1] = m1l;
+        redf[4 * warp + 2] = m2h; redf[4 * warp + 3] = m2l;
+        redd[2 * warp] = m1d; redd[2 * warp + 1] = m2d;
+        wsum[nwarps + warp] = npos;
     }
     __syncthreads();
+    // ---- warp 0: order the survivors (rank = number of better keys) and write the scratch
+    if (warp == 0) {
+        const int L = ctl[3];
+        EmsKey* dst = out.keys + (size_t)cell * kEmsMaxK;
+        for (int i = lane; i < L; i += 32) {
+            const EmsKey ki = keep[i];
+            int rk = 0;
+            for (int k = 0; k < L; ++k) rk += key_better(keep[k], ki);
+            dst[rk] = ki;
+        }
+        if (lane == 0) {
+            EmsCellInfo inf;
+            inf.L = L;
+            inf.J = J;
+            inf.is_f64 = sizeof(T) == 8;
+            int np = 0;
+            float a1h = 0.f, a1l = 0.f, a2h = 0.f, a2l = 0.f;
+            double d1 = 0.0, d2 = 0.0;
+            for (int w = 0; w < nwarps; ++w) {
+                np += wsum[nwarps + w];
+                if (all) {
+                    df_add(a1h, a1l, redf[4 * w], redf[4 * w + 1]);
+                    df_add(a2h, a2l, redf[4 * w + 2], redf[4 * w + 3]);
+                    d1 += redd[2 * w];
+                    d2 += redd[2 * w + 1];
+                }
+            }
+            inf.npos = np;
+            inf.m1h = a1h; inf.m1l = a1l; inf.m2h = a2h; inf.m2l = a2l;
+            inf.m1d = d1; inf.m2d = d2;
+            out.info[cell] = inf;
+        }
+    }
+    __syncthreads();
+}
+
+// Stage 2: one thread per cell, binary64, the definition's operation order.
+static __global__ void ems_finish_kernel(int64_t n_cells, const __grid_constant__ EmsArgs a, EmsScratch s) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= n_cells) return;
+    const EmsCellInfo inf = s.info[cell];
+    const EmsKey* top = s.keys + (size_t)cell * kEmsMaxK;
+    const int K = a.k_max, J = inf.J, L = inf.L, f64 = inf.is_f64;
+    const int Jmax = J < K ? J : K;
+    double M1 = 0.0, M2 = 0.0;
+    if (a.sum_over) {
+        if (f64) {
+            M1 = inf.m1d;
+            M2 = inf.m2d;
+        } else {
+            M1 = (double)inf.m1h + (double)inf.m1l;
+            M2 = (double)inf.m2h + (double)inf.m2l;
+        }
+    } else {
+        for (int j = 0; j < Jmax && j < L; ++j) {
+            const double e = key_value(top[j], f64);
+            M1 = __dadd_rn(M1, e);
+            M2 = __dadd_rn(M2, __dmul_rn(e, e));
+        }
+    }
+    const double neff = M2 > 0.0 ? __ddiv_rn(__dmul_rn(M1, M1), M2) : 0.0;
+    double S = 0.0;
+    if (Jmax >= 2) {
+        for (int j = 0; j < Jmax - 1 && j + 1 < L; ++j) {
+            const double e0 = key_value(top[j], f64), e1 = key_value(top[j + 1], f64);
+            if (e1 > 0.0) S = __dadd_rn(S, exp(__ddiv_rn(-__dsub_rn(__ddiv_rn(e0, e1), 1.0), a.delta)));
+        }
+        S = __ddiv_rn(S, (double)(Jmax - 1));
+    }
+    const double nclip = neff < (double)K ? neff : (double)K;
+    const double C = __dadd_rn(__ddiv_rn(__dmul_rn(a.w1, nclip), (double)K), __dmul_rn(a.w2, S));
+    const double alpha = __dadd_rn(a.alpha_min, __dmul_rn(__dsub_rn(a.alpha_max, a.alpha_min), C));
+    const double total = M1;
+    int Ks = 0;
+    double cum = 0.0;
+    if (total > 0.0) {
+        int kthr = -1;
+        double cs = 0.0;
+        for (int j = 0; j < Jmax && j < L; ++j) {
+            cs = __dadd_rn(cs, key_value(top[j], f64));
+            if (cs >= __dmul_rn(alpha, total)) { kthr = j + 1; break; }
+        }
+        if (kthr < 0) kthr = K;
+        Ks = kthr > a.k_min ? kthr : a.k_min;
+        if (Ks > K) Ks = K;
+        if (Ks > inf.npos) Ks = inf.npos;
+        if (Ks > J) Ks = J;
+        if (Ks > L) Ks = L;
+        for (int j = 0; j < Ks; ++j) cum = __dadd_rn(cum, key_value(top[j], f64));
+    }
+    a.kstar[cell] = Ks;
+    a.retained[cell] = cum;
+    int32_t* sel = a.sel + (size_t)cell * K;
+    for (int k = 0; k < K; ++k) sel[k] = k < Ks ? (int)(~top[k].q) : -1;
 }
 
 }  // namespace enufft

@@ -78,20 +78,25 @@ __device__ __forceinline__ void fft_reg(cplx<T> (&a)[N]) {
 }
 
 // Team FFT.  The team is lanes [base, base + N2) of a warp with team-relative lane t; tw is the
-// table W_N^j = e^{-2 pi i j / N}, j in [0, N).  In place through the accessor (load/store by
-// element index), natural order in and out.  Requires N1 >= N2.
-template <int N1, int N2, typename T, typename Acc>
-__device__ __forceinline__ void team_fft(Acc acc, int t, const cplx<T>* __restrict__ tw, unsigned team_mask) {
+// table W_N^j = e^{-2 pi i j / N}, j in [0, N).  Input element n comes from in.load(n); the
+// transposed intermediate goes through the workspace `wk` (N2 rows of N1 + 1 entries, the padding
+// keeping the transpose free of bank conflicts); output element k goes to out.store(k, .), natural
+// order.  The three may alias: every load of a phase completes before the next phase stores.
+// Requires N1 >= N2.
+template <int N1, int N2, typename T, typename In, typename Wk, typename Out>
+__device__ __forceinline__ void team_fft(const In& in, const Wk& wk, const Out& out, int t,
+                                         const cplx<T>* __restrict__ tw, unsigned team_mask) {
     static_assert(N1 >= N2 && N1 % N2 == 0, "team FFT split");
+    constexpr int WS = N1 + 1;
     cplx<T> a[N1];
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) a[n1] = acc.load(N2 * n1 + t);
+    for (int n1 = 0; n1 < N1; ++n1) a[n1] = in.load(N2 * n1 + t);
     fft_reg<N1, T>(a);
 #pragma unroll
     for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], tw[t * k1]);
     __syncwarp(team_mask);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) acc.store(k1 * N2 + t, a[k1]);
+    for (int k1 = 0; k1 < N1; ++k1) wk.store(t * WS + k1, a[k1]);
     __syncwarp(team_mask);
     constexpr int KK = N1 / N2;
     cplx<T> b[KK][N2];
@@ -99,16 +104,20 @@ __device__ __forceinline__ void team_fft(Acc acc, int t, const cplx<T>* __restri
     for (int kk = 0; kk < KK; ++kk) {
         const int k1 = t + kk * N2;
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) b[kk][n2] = acc.load(k1 * N2 + n2);
+        for (int n2 = 0; n2 < N2; ++n2) b[kk][n2] = wk.load(n2 * WS + k1);
         fft_reg<N2, T>(b[kk]);
     }
     __syncwarp(team_mask);
 #pragma unroll
     for (int kk = 0; kk < KK; ++kk)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) acc.store(t + kk * N2 + N1 * k2, b[kk][k2]);
+        for (int k2 = 0; k2 < N2; ++k2) out.store(t + kk * N2 + N1 * k2, b[kk][k2]);
     __syncwarp(team_mask);
 }
+
+// workspace entries a team needs for length N
+template <int N1, int N2>
+constexpr int team_ws() { return N2 * (N1 + 1); }
 
 // split of a power-of-two length over a team: N = N1 * N2 with N1 >= N2
 template <int N>
@@ -129,8 +138,17 @@ struct RowPairAcc {
     __device__ __forceinline__ void store(int i, cplx<T> v) const { r0[i] = v.re; r1[i] = v.im; }
 };
 
-// accessor: strided complex vector (shared memory); conj = true gives the inverse transform
-// through conj(FFT(conj(z)))
+// accessor: two real rows, read and written conjugated (for the inverse transform through
+// conj(FFT(conj(z))) on a row pair)
+template <typename T>
+struct RowPairConjAcc {
+    T* r0;
+    T* r1;
+    __device__ __forceinline__ cplx<T> load(int i) const { return {r0[i], -r1[i]}; }
+    __device__ __forceinline__ void store(int i, cplx<T> v) const { r0[i] = v.re; r1[i] = -v.im; }
+};
+
+// accessor: strided complex vector (shared memory); Conj = true reads and writes conjugated
 template <typename T, bool Conj>
 struct StridedAcc {
     cplx<T>* p;

@@ -7,14 +7,21 @@
 //      exact binary32 transforms, the mask test (binary32 with a certified margin, binary64 when
 //      a sample is closer than the margin to the boundary), c_q = w_q h_q / |D|;
 //   2. spread c_q with the exponential-of-semicircle kernel onto a real n_f x n_f grid held in
-//      shared memory with a halo (so no per-tap wrap arithmetic), then fold the halo (periodic);
+//      shared memory with a halo (so no per-tap wrap arithmetic), then fold the halo (periodic).
+//      The binary32 path accumulates in 32-bit fixed point with native integer shared-memory
+//      reductions: a per-cell pre-pass bounds every node by S = sum |c_q| (the kernel is <= 1),
+//      so each tap is rounded to an integer at scale 2^30 / S and no partial sum can overflow;
+//      integer sums are also independent of the order in which samples arrive (bit-reproducible);
 //   3. 2-D FFT: real rows in pairs (one complex FFT per pair, split by conjugate symmetry),
 //      then the P/2 + 1 needed columns, each by a team of lanes (fft.cuh);
-//   4. deconvolve by 1/(Phi(m) Phi(n)), crop to m, n in [-P/2, P/2) (Hermitian fill of m < 0),
-//      stage the P x P spectrum in shared memory;
-//   5. optionally EMS on the staged spectrum (ems.cuh), then one coalesced 16-byte-vector store.
+//   4. deconvolve by 1/(Phi(m) Phi(n)) and crop to m, n in [-P/2, P/2) (Hermitian fill of m < 0)
+//      straight out of the column transforms into a staged P x P spectrum;
+//   5. optionally rank the staged spectrum's mode pairs for EMS (ems.cuh, stage 1), then one
+//      coalesced 16-byte-vector store of the spectrum.
 // The grid origin is the paper's x' = u + H (App. A), so no phase correction is needed.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "ems.cuh"
@@ -23,6 +30,10 @@
 namespace enufft {
 
 constexpr int kMaxHalf = 64;   // P/2 <= 64
+
+#ifndef ENUFFT_FWD_MINB
+#define ENUFFT_FWD_MINB 2   // co-resident 512-thread blocks per SM of the binary32 fused kernels
+#endif
 
 template <typename T>
 struct FwdArgs {
@@ -44,6 +55,7 @@ struct FwdArgs {
     double beta;                           // ES shape (binary64 direct evaluation)
     int do_ems;
     EmsArgs ems;
+    EmsScratch ems_out;   // stage-1 EMS results (top keys, counts) per cell
 };
 
 template <typename T, int NF, int W>
@@ -55,16 +67,24 @@ struct FwdCfg {
     static constexpr int NT = NF >= 128 ? 512 : 256;          // threads per block
     // co-resident blocks the register budget is sized for (two 512-thread blocks per SM when the
     // shared-memory footprint allows it, so one block's FFT overlaps the other's spreading)
-    static constexpr int MINB = (sizeof(T) == 4 && NF <= 128) ? 2 : 1;
+    static constexpr int MINB = (sizeof(T) == 4 && NF <= 128) ? ENUFFT_FWD_MINB : 1;
     static constexpr int NWARPS = NT / 32;
     static constexpr int N1 = FftSplit<NF>::N1, N2 = FftSplit<NF>::N2;
-    static constexpr int R_EMS = ((NF / 4) * (NF / 4) * 2 / NWARPS + 31) / 32;   // >= J*/nwarps/32
+    static constexpr int WS_TEAM = team_ws<N1, N2>();          // workspace per team (complex)
+    static constexpr int R_EMS = ((NF / 4) * (NF / 4) * 2 + NT - 1) / NT;   // >= J* / threads
     static constexpr size_t grid_bytes = sizeof(T) * (size_t)GR * GS;
     static constexpr size_t c1_bytes_min = sizeof(cplx<T>) * (size_t)NF * C1S_MAX;
     static constexpr size_t ems_bytes = ems_smem_bytes(NWARPS, kEmsMaxK);
     static constexpr size_t c1_bytes = c1_bytes_min > ems_bytes ? c1_bytes_min : ems_bytes;
     static constexpr size_t tw_bytes = sizeof(cplx<T>) * NF;
-    static constexpr size_t smem_bytes = grid_bytes + c1_bytes + tw_bytes + sizeof(CellConst) + 64;
+    static constexpr size_t tail_bytes = sizeof(CellConst) + 16 + sizeof(T) * (kMaxHalf + 1) + 4 * NWARPS + 16;
+    static constexpr size_t smem_bytes = grid_bytes + c1_bytes + tw_bytes + tail_bytes;
+    // after the row pass the grid memory holds the staged P x P spectrum followed by the column
+    // teams' workspaces
+    static constexpr size_t stage_ws_bytes =
+        sizeof(cplx<T>) * ((size_t)(NF / 2) * (NF / 2) + (size_t)C1S_MAX * WS_TEAM);
+    static_assert(stage_ws_bytes <= grid_bytes, "staging + column workspace must fit in the grid memory");
+    static_assert(GS >= WS_TEAM && GS >= NF + W + 2, "row workspace must fit in a padded row");
 };
 
 __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
@@ -91,67 +111,70 @@ __device__ __forceinline__ bool window_f64(const CellConst& cc, double x, double
 }
 
 // binary32 window test with a certified margin: returns 1 inside, 0 outside, -1 undecided
-__device__ __forceinline__ int window_f32(const CellConst& cc, float ux, float uy) {
-    const float tau = cc.tau;
+__device__ __forceinline__ int window_f32(const FastFrame& ff, const float4* __restrict__ edge, float ux, float uy) {
+    const float tau = ff.tau;
     int unsure = 0;
-    const float bx = fabsf(ux) - cc.Hf, by = fabsf(uy) - cc.Hf;
+    const float bx = fabsf(ux) - ff.Hf, by = fabsf(uy) - ff.Hf;
     if (bx > tau || by > tau) return 0;
     unsure |= (bx > -tau) | (by > -tau);
-    if (cc.mask == 0) {
-        for (int i = 0; i < cc.nv; ++i) {
-            const float f = __fmaf_rn(cc.enx[i], ux, __fmaf_rn(cc.eny[i], uy, -cc.ed[i]));
-            if (f > tau) return 0;
-            unsure |= f > -tau;
+    if (ff.mask == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i < ff.nv) {
+                const float4 e = edge[i];
+                const float f = __fmaf_rn(e.x, ux, __fmaf_rn(e.y, uy, -e.z));
+                if (f > tau) return 0;
+                unsure |= f > -tau;
+            }
         }
-    } else if (cc.mask == 2) {
-        const float f = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, -cc.Hf * cc.Hf));
-        const float t2 = 4.0f * tau * cc.Hf;
+    } else if (ff.mask == 2) {
+        const float f = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, -ff.Hf * ff.Hf));
+        const float t2 = 4.0f * tau * ff.Hf;
         if (f > t2) return 0;
         unsure |= f > -t2;
     }
     return unsure ? -1 : 1;
 }
 
-// Horner evaluation of the W kernel pieces at u in [-1, 1]
+// Horner evaluation of the W kernel pieces at u in [-1, 1] (DEG coefficients, compile time)
 template <int W>
 __device__ __forceinline__ void kernel_pieces(const KernelPoly& kp, float u, float (&v)[W]) {
+    constexpr int DEG = poly_deg(W);
 #pragma unroll
-    for (int i = 0; i < W; ++i) v[i] = kp.c[i][kMaxDeg - 1];
+    for (int i = 0; i < W; ++i) v[i] = kp.c[i][DEG - 1];
 #pragma unroll
-    for (int d = kMaxDeg - 2; d >= 0; --d) {
-        if (d < kp.deg) {   // deg is uniform across the grid; unused leading pieces are zero
+    for (int d = DEG - 2; d >= 0; --d)
 #pragma unroll
-            for (int i = 0; i < W; ++i) v[i] = __fmaf_rn(v[i], u, kp.c[i][d]);
-        }
-    }
+        for (int i = 0; i < W; ++i) v[i] = __fmaf_rn(v[i], u, kp.c[i][d]);
 }
 
 // Per-sample setup shared by spreading and interpolation (binary32 path): window test, first
 // node r0 of each dimension and the W kernel values there.  Returns false for samples outside
 // the window (or non-finite ones, which also latch ST_NONFINITE).
 template <int NF, int W>
-__device__ __forceinline__ bool prep_f32(const CellConst& cc, const KernelPoly& kp, float px, float py,
-                                         int& r0x, int& r0y, float (&kx)[W], float (&ky)[W], unsigned* status) {
+__device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __restrict__ edge, const CellConst& cc,
+                                         const KernelPoly& kp, float px, float py, int& r0x, int& r0y,
+                                         float (&kx)[W], float (&ky)[W], unsigned* status) {
     if (!(isfinite(px) && isfinite(py))) {
         atomicOr(status, ST_NONFINITE);
         return false;
     }
     float uxh, uxl, uyh, uyl;
-    two_diff(px, cc.cxh, uxh, uxl);
-    uxl = __fsub_rn(uxl, cc.cxl);
-    two_diff(py, cc.cyh, uyh, uyl);
-    uyl = __fsub_rn(uyl, cc.cyl);
-    int win = window_f32(cc, uxh + uxl, uyh + uyl);
+    two_diff(px, ff.cxh, uxh, uxl);
+    uxl = __fsub_rn(uxl, ff.cxl);
+    two_diff(py, ff.cyh, uyh, uyl);
+    uyl = __fsub_rn(uyl, ff.cyl);
+    int win = window_f32(ff, edge, uxh + uxl, uyh + uyl);
     if (win < 0) win = window_f64(cc, (double)px, (double)py);
     if (!win) return false;
     // grid coordinate s = u * (n_f / L) + n_f / 2; first node r0 = ceil(s - W/2);
     // t = r0 - s + W/2 in [0, 1) from the hi/lo pieces (one rounding at magnitude < 1)
-    const float sx = __fmaf_rn(uxh, cc.sch, 0.5f * NF), sy = __fmaf_rn(uyh, cc.sch, 0.5f * NF);
+    const float sx = __fmaf_rn(uxh, ff.sch, 0.5f * NF), sy = __fmaf_rn(uyh, ff.sch, 0.5f * NF);
     r0x = (int)ceilf(sx - 0.5f * W);
     r0y = (int)ceilf(sy - 0.5f * W);
-    const float corrx = __fmaf_rn(uxh, cc.scl, uxl * cc.sch), corry = __fmaf_rn(uyh, cc.scl, uyl * cc.sch);
-    const float tx = __fmaf_rn(-uxh, cc.sch, (float)(r0x - NF / 2) + 0.5f * W) - corrx;
-    const float ty = __fmaf_rn(-uyh, cc.sch, (float)(r0y - NF / 2) + 0.5f * W) - corry;
+    const float corrx = __fmaf_rn(uxh, ff.scl, uxl * ff.sch), corry = __fmaf_rn(uyh, ff.scl, uyl * ff.sch);
+    const float tx = __fmaf_rn(-uxh, ff.sch, (float)(r0x - NF / 2) + 0.5f * W) - corrx;
+    const float ty = __fmaf_rn(-uyh, ff.sch, (float)(r0y - NF / 2) + 0.5f * W) - corry;
     kernel_pieces<W>(kp, __fmaf_rn(2.0f, tx, -1.0f), kx);
     kernel_pieces<W>(kp, __fmaf_rn(2.0f, ty, -1.0f), ky);
     return true;
@@ -179,17 +202,19 @@ __device__ __forceinline__ bool prep_f64(const CellConst& cc, double beta, doubl
     return true;
 }
 
-// shared-memory float reduction with a compile-time immediate offset
+// shared-memory 32-bit integer reduction (two's complement) with a compile-time immediate offset
 template <int OFF>
-__device__ __forceinline__ void red_smem(unsigned addr, float v) {
-    asm volatile("red.shared.add.f32 [%0+%2], %1;" ::"r"(addr), "f"(v), "n"(OFF * 4));
+__device__ __forceinline__ void red_smem(unsigned addr, int v) {
+    asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF * 4));
 }
 
+// the W x W taps of one sample: c (already multiplied by the cell's fixed-point scale) times the
+// separable kernel, rounded to the nearest integer
 template <int W, int GS, int J = 0, int I = 0>
 __device__ __forceinline__ void spread_taps(unsigned addr, const float (&kx)[W], const float (&ky)[W], float c) {
     if constexpr (J < W) {
         if constexpr (I < W) {
-            red_smem<J * GS + I>(addr, (c * ky[J]) * kx[I]);
+            red_smem<J * GS + I>(addr, __float2int_rn((c * ky[J]) * kx[I]));
             spread_taps<W, GS, J, I + 1>(addr, kx, ky, c);
         } else {
             spread_taps<W, GS, J + 1, 0>(addr, kx, ky, c);
@@ -197,14 +222,15 @@ __device__ __forceinline__ void spread_taps(unsigned addr, const float (&kx)[W],
     }
 }
 
-// spread one sample (binary32 path); g points at the padded grid
+// spread one sample (binary32 path) into the fixed-point grid g (scale: the cell's 2^30 / S)
 template <int NF, int W, int GS, int HO>
-__device__ __forceinline__ void spread_f32(float* __restrict__ g, const CellConst& cc, const KernelPoly& kp,
-                                           float px, float py, float ph, float pw, unsigned* status) {
+__device__ __forceinline__ void spread_f32(int* __restrict__ g, const FastFrame& ff, const float4* __restrict__ edge,
+                                           const CellConst& cc, const KernelPoly& kp, float px, float py, float ph,
+                                           float pw, float scale, unsigned* status) {
     int r0x, r0y;
     float kx[W], ky[W];
-    if (!prep_f32<NF, W>(cc, kp, px, py, r0x, r0y, kx, ky, status)) return;
-    const float c = pw * ph * cc.inv_area;
+    if (!prep_f32<NF, W>(ff, edge, cc, kp, px, py, r0x, r0y, kx, ky, status)) return;
+    const float c = pw * ph * ff.inv_area * scale;
     if (!isfinite(c)) {
         atomicOr(status, ST_NONFINITE);
         return;
@@ -241,6 +267,60 @@ struct StagedSpec {
     __device__ __forceinline__ cplx<T> get(int m, int n) const { return s[(n + half) * P + (m + half)]; }
 };
 
+// two fixed-point grid rows read as one complex row z = (row0 + i row1) / scale
+struct FixedRowPairAcc {
+    const int* r0;
+    const int* r1;
+    float inv_scale;
+    __device__ __forceinline__ cplx<float> load(int i) const {
+        return {(float)r0[i] * inv_scale, (float)r1[i] * inv_scale};
+    }
+};
+
+// per-thread sum of |w_q h_q| / |D| over a cell's samples, reduced over the block (finite terms only)
+template <int NT>
+__device__ __forceinline__ float cell_abs_sum(const float* __restrict__ h, const float* __restrict__ w, int64_t q0,
+                                              int64_t q1, float inv_area, float* red) {
+    float s = 0.0f;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += NT) {
+        const float v = fabsf(w[q] * h[q]);
+        s += (v <= 3.0e38f) ? v : 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += red[i];
+    return t * inv_area;
+}
+
+// contiguous complex workspace accessor
+template <typename T>
+struct PlainAcc {
+    cplx<T>* p;
+    __device__ __forceinline__ cplx<T> load(int i) const { return p[i]; }
+    __device__ __forceinline__ void store(int i, cplx<T> v) const { p[i] = v; }
+};
+
+// output of a column transform (column m, element k = n mod n_f): deconvolve and place it in the
+// staged P x P spectrum, directly at (m, n) and by Hermitian symmetry at (-m, -n)
+template <typename T, int NF>
+struct DeconvStageOut {
+    cplx<T>* stage;
+    const T* inv_phi;
+    int m, P, half;
+    __device__ __forceinline__ void store(int k, cplx<T> z) const {
+        const int n = k < NF / 2 ? k : k - NF;
+        if (n < -half || n > half) return;
+        const T f = inv_phi[m] * inv_phi[n < 0 ? -n : n];
+        const cplx<T> v{z.re * f, z.im * f};
+        if (m < half && n < half) stage[(n + half) * P + (m + half)] = v;
+        if (m >= 1 && n > -half) stage[(half - n) * P + (half - m)] = cconj(v);
+    }
+};
+
 template <typename T, int NF, int W>
 __global__ void __launch_bounds__(FwdCfg<T, NF, W>::NT, FwdCfg<T, NF, W>::MINB)
 type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
@@ -252,10 +332,14 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
     cplx<T>* stw = reinterpret_cast<cplx<T>*>(smem + CF::grid_bytes + CF::c1_bytes);
     CellConst* scc = reinterpret_cast<CellConst*>(smem + CF::grid_bytes + CF::c1_bytes + CF::tw_bytes);
     int* sticket = reinterpret_cast<int*>(scc + 1);
+    T* sinv = reinterpret_cast<T*>(sticket + 4);
+    float* sred = reinterpret_cast<float*>(sinv + kMaxHalf + 1);
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int P = a.P, half = P / 2, C1S = half + 1;
     for (int i = tid; i < NF; i += CF::NT) stw[i] = a.twiddle[i];
+    for (int i = tid; i <= half; i += CF::NT) sinv[i] = a.inv_phi[i];
+    float inv_scale = 1.0f;   // fixed-point scale of the current cell (binary32 path)
 
     for (;;) {
         if (tid == 0) *sticket = (int)atomicAdd(a.ticket, 1u);
@@ -264,9 +348,9 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
         if (tk >= a.n_work) break;
         const int cell = a.order[tk];
         {   // per-cell constants into shared memory; zero the padded grid
-            const int* src = reinterpret_cast<const int*>(a.cells + cell);
-            int* dst = reinterpret_cast<int*>(scc);
-            for (int i = tid; i < (int)(sizeof(CellConst) / 4); i += CF::NT) dst[i] = src[i];
+            const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
+            int4* dst = reinterpret_cast<int4*>(scc);
+            for (int i = tid; i < (int)(sizeof(CellConst) / 16); i += CF::NT) dst[i] = src[i];
             float4* g4 = reinterpret_cast<float4*>(sgrid);
             const int n4 = (int)(CF::grid_bytes / 16);
             for (int i = tid; i < n4; i += CF::NT) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -277,40 +361,47 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
         if (cc.valid) {
             const int64_t q0 = a.offsets[cell], q1 = a.offsets[cell + 1];
             int64_t q = q0 + tid;
-            for (; q + CF::NT < q1; q += 2 * CF::NT) {   // two samples per thread in flight
-                const T x0 = a.x[q], y0 = a.y[q], h0 = a.h[q], w0 = a.w[q];
-                const T x1 = a.x[q + CF::NT], y1 = a.y[q + CF::NT], h1 = a.h[q + CF::NT], w1 = a.w[q + CF::NT];
-                if constexpr (sizeof(T) == 4) {
-                    spread_f32<NF, W, GS, HO>(sgrid, cc, a.poly, x0, y0, h0, w0, a.status);
-                    spread_f32<NF, W, GS, HO>(sgrid, cc, a.poly, x1, y1, h1, w1, a.status);
-                } else {
-                    spread_f64<NF, W, GS, HO>(sgrid, cc, a.beta, x0, y0, h0, w0, a.status);
-                    spread_f64<NF, W, GS, HO>(sgrid, cc, a.beta, x1, y1, h1, w1, a.status);
+            if constexpr (sizeof(T) == 4) {
+                const FastFrame ff = fast_frame(cc);
+                // fixed-point scale: every node of the grid is bounded by S = sum |c_q|
+                const float S = cell_abs_sum<CF::NT>(a.h, a.w, q0, q1, ff.inv_area, sred);
+                const float scale = S > 0x1p-96f ? 0x1p30f / S : 0x1p126f;
+                inv_scale = 1.0f / scale;
+                int* sgi = reinterpret_cast<int*>(sgrid);
+                // the next sample's loads are issued before the current one is spread
+                float x0 = 0.f, y0 = 0.f, h0 = 0.f, w0 = 0.f;
+                if (q < q1) { x0 = a.x[q]; y0 = a.y[q]; h0 = a.h[q]; w0 = a.w[q]; }
+                for (; q < q1; q += CF::NT) {
+                    const int64_t qn = q + CF::NT;
+                    float x1 = 0.f, y1 = 0.f, h1 = 0.f, w1 = 0.f;
+                    if (qn < q1) { x1 = a.x[qn]; y1 = a.y[qn]; h1 = a.h[qn]; w1 = a.w[qn]; }
+                    spread_f32<NF, W, GS, HO>(sgi, ff, cc.edge, cc, a.poly, x0, y0, h0, w0, scale, a.status);
+                    x0 = x1; y0 = y1; h0 = h1; w0 = w1;
                 }
-            }
-            if (q < q1) {
-                if constexpr (sizeof(T) == 4)
-                    spread_f32<NF, W, GS, HO>(sgrid, cc, a.poly, a.x[q], a.y[q], a.h[q], a.w[q], a.status);
-                else
+            } else {
+                for (; q < q1; q += CF::NT)
                     spread_f64<NF, W, GS, HO>(sgrid, cc, a.beta, a.x[q], a.y[q], a.h[q], a.w[q], a.status);
             }
         } else if (tid == 0) {
             atomicOr(a.status, ST_BADCELL);
         }
         __syncthreads();
-        // ---- periodic fold of the halo: columns first (all padded rows), then rows
+        // ---- periodic fold of the halo: columns first (all padded rows), then rows (exact integer
+        // adds on the binary32 path's fixed-point grid)
+        using Acc = typename std::conditional<sizeof(T) == 4, int, double>::type;
+        Acc* sacc = reinterpret_cast<Acc*>(sgrid);
         for (int i = tid; i < GR * (GR - NF); i += CF::NT) {
             const int r = i / (GR - NF), k = i % (GR - NF);
             const int c = k < HO ? k : k + NF;              // halo column
             const int cw = k < HO ? k + NF : k;             // its periodic image inside the core
-            sgrid[r * GS + cw] += sgrid[r * GS + c];
+            sacc[r * GS + cw] += sacc[r * GS + c];
         }
         __syncthreads();
         for (int i = tid; i < (GR - NF) * NF; i += CF::NT) {
             const int k = i / NF, c = HO + i % NF;
             const int r = k < HO ? k : k + NF;
             const int rw = k < HO ? k + NF : k;
-            sgrid[rw * GS + c] += sgrid[r * GS + c];
+            sacc[rw * GS + c] += sacc[r * GS + c];
         }
         __syncthreads();
         // ---- step 3a: FFT of the rows, two real rows per complex transform; keep m = 0..P/2
@@ -318,9 +409,17 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             const int team = tid / N2, t = tid % N2;
             const unsigned tmask = ((1u << N2) - 1u) << (lane & ~(N2 - 1));
             if (team < NF / 2) {
-                T* r0 = sgrid + (HO + 2 * team) * GS + HO;
+                T* r0 = sgrid + (HO + 2 * team) * GS;
                 T* r1 = r0 + GS;
-                team_fft<N1, N2, T>(RowPairAcc<T>{r0, r1}, t, stw, tmask);
+                // input in the core columns, transposed workspace and output from column 0
+                if constexpr (sizeof(T) == 4) {
+                    const int* i0 = reinterpret_cast<const int*>(r0) + HO;
+                    team_fft<N1, N2, T>(FixedRowPairAcc{i0, i0 + GS, inv_scale}, RowPairAcc<T>{r0, r1},
+                                        RowPairAcc<T>{r0, r1}, t, stw, tmask);
+                } else {
+                    team_fft<N1, N2, T>(RowPairAcc<T>{r0 + HO, r1 + HO}, RowPairAcc<T>{r0, r1}, RowPairAcc<T>{r0, r1},
+                                        t, stw, tmask);
+                }
                 for (int m = t; m <= half; m += N2) {
                     const int mn = (NF - m) & (NF - 1);
                     const T zr = r0[m], zi = r1[m], wr = r0[mn], wi = r1[mn];
@@ -330,28 +429,22 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             }
         }
         __syncthreads();
-        // ---- step 3b: FFT of the columns m = 0..P/2
+        // ---- step 3b + 4: FFT of the columns m = 0..P/2, deconvolved and cropped into the stage
+        cplx<T>* stage = reinterpret_cast<cplx<T>*>(sgrid);
         {
             const int team = tid / N2, t = tid % N2;
             const unsigned tmask = ((1u << N2) - 1u) << (lane & ~(N2 - 1));
-            if (team <= half) team_fft<N1, N2, T>(StridedAcc<T, false>{sC1 + team, C1S}, t, stw, tmask);
-        }
-        __syncthreads();
-        // ---- step 4: deconvolve, crop, Hermitian fill, stage P x P in the (now free) grid memory
-        cplx<T>* stage = reinterpret_cast<cplx<T>*>(sgrid);
-        for (int i = tid; i < (half + 1) * (P + 1); i += CF::NT) {
-            const int m = i % (half + 1), n = i / (half + 1) - half;
-            const T f = a.inv_phi[m] * a.inv_phi[n < 0 ? -n : n];
-            const cplx<T> z = sC1[((n + NF) & (NF - 1)) * C1S + m];
-            const cplx<T> v{z.re * f, z.im * f};
-            if (m < half && n < half) stage[(n + half) * P + (m + half)] = v;
-            if (m >= 1 && n > -half) stage[(half - n) * P + (half - m)] = cconj(v);
+            if (team <= half) {
+                cplx<T>* wk = stage + (size_t)(NF / 2) * (NF / 2) + (size_t)team * CF::WS_TEAM;
+                team_fft<N1, N2, T>(StridedAcc<T, false>{sC1 + team, C1S}, PlainAcc<T>{wk},
+                                    DeconvStageOut<T, NF>{stage, sinv, team, P, half}, t, stw, tmask);
+            }
         }
         __syncthreads();
         // ---- step 5: EMS on the staged spectrum (shared scratch in the free half-spectrum area)
         if (a.do_ems)
-            ems_block<T, CF::R_EMS>(StagedSpec<T>{stage, P, half}, P, cell, a.ems,
-                                    reinterpret_cast<unsigned char*>(sC1));
+            ems_rank_block<T, CF::R_EMS>(StagedSpec<T>{stage, P, half}, P, cell, a.ems, a.ems_out,
+                                         reinterpret_cast<unsigned char*>(sC1));
         {   // coalesced 16-byte stores of the P x P spectrum
             const float4* s4 = reinterpret_cast<const float4*>(stage);
             float4* d4 = reinterpret_cast<float4*>(a.coeffs + (size_t)cell * P * P * 2);

@@ -116,15 +116,13 @@ __global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__ nverts
             nx = cc.orient * dy / len;   // outward normal of a counter-clockwise edge is (dy, -dx)
             ny = -cc.orient * dx / len;
         }
-        cc.enx[i] = (float)nx;
-        cc.eny[i] = (float)ny;
-        cc.ed[i] = (float)(nx * cc.ux[i] + ny * cc.uy[i]);
+        cc.edge[i] = make_float4((float)nx, (float)ny, (float)(nx * cc.ux[i] + ny * cc.uy[i]), 0.0f);
     }
     out[j] = cc;
 }
 
 // ---------------------------------------------------------------------------------------------
-// standalone EMS: one block per cell, energies read from the stored spectrum
+// standalone EMS stage 1: one block per cell, energies read from the stored spectrum
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct GlobalSpec {
@@ -134,11 +132,11 @@ struct GlobalSpec {
 };
 
 template <typename T, int R>
-__global__ void __launch_bounds__(512) ems_kernel(const cplx<T>* __restrict__ coeffs, int P, int64_t n_cells,
-                                                  const __grid_constant__ EmsArgs a) {
+__global__ void __launch_bounds__(512) ems_rank_kernel(const cplx<T>* __restrict__ coeffs, int P, int64_t n_cells,
+                                                       const __grid_constant__ EmsArgs a, EmsScratch out) {
     extern __shared__ __align__(16) unsigned char smem[];
     for (int64_t cell = blockIdx.x; cell < n_cells; cell += gridDim.x)
-        ems_block<T, R>(GlobalSpec<T>{coeffs + (size_t)cell * P * P, P, P / 2}, P, (int)cell, a, smem);
+        ems_rank_block<T, R>(GlobalSpec<T>{coeffs + (size_t)cell * P * P, P, P / 2}, P, (int)cell, a, out, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
