@@ -168,6 +168,27 @@ enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs,
  * work already queued on the old stream is not waited for.  NULL selects the legacy default. */
 enufft_status enufft_set_stream(enufft_plan plan, void *cuda_stream);
 
+/*
+ * enufft_ems without a plan and without any device allocation (the paper has no counterpart; it
+ * is a deployment convenience).  For callers that cannot allocate device memory when they need
+ * the selection -- where a cudaMalloc would synchronise the device inside a latency-bound
+ * pipeline, where another allocator owns the device memory, or in plug-ins that may not own
+ * device memory.  Same arguments and results as enufft_ems for binary32 (complex64) spectra of
+ * n_cells cells with P = modes, on the given stream.
+ *   - n_cells must not exceed 2048 (the fixed scratch): larger batches return ENUFFT_ERR_ARG
+ *     with a message and launch nothing.
+ *   - The scratch is one static device array (about 2.2 MB) held by every GPU that loads the
+ *     library until the process exits, shared by all calls: calls whose work overlaps on the GPU
+ *     (different streams, or different host threads) race on it and must be serialised by the
+ *     caller.  Nothing in it needs to start at zero.
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ */
+enufft_status enufft_ems_noalloc(int modes, int64_t n_cells, const void *d_coeffs,
+                                 const double *d_mode_weights, int mode_weights_per_cell,
+                                 const enufft_ems_params *params, int32_t *d_kstar, int32_t *d_sel,
+                                 double *d_retained_power, void *cuda_stream);
+
 /* Synchronise the plan's stream and report (then clear) any latched device-side condition. */
 enufft_status enufft_sync_status(enufft_plan plan);
 

@@ -92,6 +92,8 @@ struct enufft_plan_s {
 
 static thread_local std::string g_last_error;
 
+void enufft::set_thread_error(const std::string& msg) { g_last_error = msg; }
+
 static enufft_status fail(enufft_plan p, enufft_status st, const std::string& msg) {
     if (p)
         p->err = msg;

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "adjoint.cuh"
 #include "forward.cuh"
 
@@ -20,5 +22,8 @@ cudaError_t launch_type1(const FwdArgs<float>& a, int nf, int w, int grid, cudaS
 cudaError_t launch_type1(const FwdArgs<double>& a, int nf, int w, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs<float>& a, int nf, int w, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cudaStream_t s);
+
+// Record the calling thread's last error text (read back by enufft_last_error(NULL)).
+void set_thread_error(const std::string& msg);
 
 }  // namespace enufft

@@ -32,7 +32,7 @@ __device__ inline int clip_side(int n, const double* x, const double* y, int axi
     return m;
 }
 
-__global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__ nverts, const double* __restrict__ verts,
+static __global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__ nverts, const double* __restrict__ verts,
                              double eta, int mask, int nf, CellConst* __restrict__ out) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n_cells) return;
