@@ -110,9 +110,9 @@ __device__ __forceinline__ double key_value(const EmsKey& k, int is_f64) {
     return is_f64 ? __longlong_as_double((long long)k.e) : (double)__uint_as_float((unsigned)k.e);
 }
 
-// shared-memory scratch of stage 1: digit histogram, selected keys, reductions
+// shared-memory scratch of stage 1: digit histogram, surviving keys, reductions
 __host__ __device__ constexpr size_t ems_smem_bytes(int nwarps, int k_max) {
-    return sizeof(unsigned) * 256 + sizeof(EmsKey) * (size_t)k_max + sizeof(float) * 4 * nwarps +
+    return sizeof(unsigned) * 256 + sizeof(EmsKey) * (size_t)(k_max > 64 ? k_max : 64) + sizeof(float) * 4 * nwarps +
            sizeof(double) * 2 * nwarps + sizeof(int) * (2 * nwarps + 8) + 64;
 }
 
@@ -138,10 +138,13 @@ __device__ __forceinline__ void ems_mode_of(int j, int lim, int row, int dc_firs
 // the block must call it; it ends with a __syncthreads().
 //
 // The K_max largest energies are found by a most-significant-digit radix select on the energy
-// bits (8-bit digits, one shared-memory histogram pass per digit), which yields the K-th largest
-// value T; the keys above T are kept, and of the keys equal to T those with the lowest pair
-// index, found by a block prefix count in candidate order.  One warp then orders the <= K_max
-// survivors by (energy desc, index asc).
+// bits (8-bit digits, one shared-memory histogram pass per digit).  As soon as the keys at or
+// above the current digit prefix number at most kEmsCand, they are all kept and one warp ranks
+// them exactly by (energy desc, index asc); otherwise the select runs to the last digit, which
+// yields the K-th largest value T, and of the keys equal to T those with the lowest pair index
+// are kept (block prefix count in candidate order).
+constexpr int kEmsCand = 64;
+
 template <typename T, int R, typename Spec>
 __device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs& a, const EmsScratch& out,
                                unsigned char* smem) {
@@ -154,56 +157,67 @@ __device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs&
     const int J = (lim > 0 ? lim + lim * row : 0) + dc;
     const int K = a.k_max;
     unsigned* hist = reinterpret_cast<unsigned*>(smem);
-    EmsKey* keep = reinterpret_cast<EmsKey*>(hist + 256);
-    float* redf = reinterpret_cast<float*>(keep + K);
+    EmsKey* keep = reinterpret_cast<EmsKey*>(hist + 256);     // kEmsCand entries
+    float* redf = reinterpret_cast<float*>(keep + kEmsCand);
     double* redd = reinterpret_cast<double*>(redf + 4 * nwarps);
-    int* wsum = reinterpret_cast<int*>(redd + 2 * nwarps);     // [nwarps] warp totals
-    int* ctl = wsum + 2 * nwarps;                             // [0] prefix lo, [1] prefix hi, [2] remaining, [3] kept
+    int* wsum = reinterpret_cast<int*>(redd + 2 * nwarps);     // [2 * nwarps]
+    int* ctl = wsum + 2 * nwarps;                             // [0] digit, [2] remaining, [3] kept, [4] stop
     const double* Wc = a.W ? a.W + (a.w_per_cell ? (size_t)cell * P * P : 0) : nullptr;
     const bool all = a.sum_over != 0;
 
-    // ---- energies, candidates j = tid * R + r (contiguous per thread)
+    // ---- energies, candidates j = tid * R + r (contiguous per thread, modes walked without division)
     U u[R];
+    int pj[R];
     float m1h = 0.f, m1l = 0.f, m2h = 0.f, m2l = 0.f;
     double m1d = 0.0, m2d = 0.0;
     int npos = 0;
+    {
+        int m = 0, n = 0;
+        const int j0 = tid * R;
+        if (j0 < J) ems_mode_of(j0, lim, row, dc, m, n);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int j = tid * R + r;
-        u[r] = 0;
-        if (j < J) {
-            int m, n;
-            ems_mode_of(j, lim, row, dc, m, n);
-            const bool isdc = (m == 0 && n == 0);
-            const int p = (n + half) * P + (m + half);
-            const T e = EN::pair(spec.get(m, n), spec.get(-m, -n), isdc, Wc ? Wc[p] : 1.0, Wc != nullptr);
-            u[r] = (U)EN::bits(e);
-            npos += e > T(0);
-            if (all) {
-                if constexpr (sizeof(T) == 4) {
-                    const float sq = __fmul_rn(e, e), sqe = __fmaf_rn(e, e, -sq);
-                    df_add(m1h, m1l, e, 0.f);
-                    df_add(m2h, m2l, sq, sqe);
-                } else {
-                    m1d += e;
-                    m2d += e * e;
+        for (int r = 0; r < R; ++r) {
+            const int j = j0 + r;
+            u[r] = 0;
+            pj[r] = 0;
+            if (j < J) {
+                const bool isdc = (m == 0 && n == 0);
+                const int p = (n + half) * P + (m + half);
+                const T e = EN::pair(spec.get(m, n), spec.get(-m, -n), isdc, Wc ? Wc[p] : 1.0, Wc != nullptr);
+                u[r] = (U)EN::bits(e);
+                pj[r] = p;
+                npos += e > T(0);
+                if (all) {
+                    if constexpr (sizeof(T) == 4) {
+                        const float sq = __fmul_rn(e, e), sqe = __fmaf_rn(e, e, -sq);
+                        df_add(m1h, m1l, e, 0.f);
+                        df_add(m2h, m2l, sq, sqe);
+                    } else {
+                        m1d += e;
+                        m2d += e * e;
+                    }
+                }
+                // next candidate in enumeration order
+                if (isdc) {
+                    m = 1; n = 0;
+                } else if (++m > lim) {
+                    m = -lim; ++n;
                 }
             }
         }
     }
     const int Kt = K < J ? K : J;   // keys to keep
-    // ---- radix select of the Kt-th largest energy (digits from the most significant)
+    // ---- radix select (digits from the most significant), with early exit
     U prefix = 0, pmask = 0;
-    int remaining = Kt;
+    int remaining = Kt, stop = 0;
+    if (tid == 0) ctl[3] = 0;
     for (int d = NDIG - 1; d >= 0 && Kt > 0; --d) {
         const int shift = 8 * d;
         for (int i = tid; i < 256; i += nt) hist[i] = 0;
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int j = tid * R + r;
-            if (j < J && (u[r] & pmask) == prefix) atomicAdd(&hist[(unsigned)(u[r] >> shift) & 255u], 1u);
-        }
+        for (int r = 0; r < R; ++r)
+            if (tid * R + r < J && (u[r] & pmask) == prefix) atomicAdd(&hist[(unsigned)(u[r] >> shift) & 255u], 1u);
         __syncthreads();
         if (warp == 0) {
             // lane l owns digits 255 - 8l .. 248 - 8l (descending); exclusive scan from the top
@@ -218,12 +232,13 @@ __device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs&
             }
             unsigned before = incl - tot;   // keys with a larger digit than this lane's first digit
             int found = -1;
-            unsigned above = 0;
+            unsigned above = 0, inbin = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 if (found < 0 && before + c8[k] >= (unsigned)remaining && before < (unsigned)remaining) {
                     found = 255 - 8 * lane - k;
                     above = before;
+                    inbin = c8[k];
                 }
                 before += c8[k];
             }
@@ -231,43 +246,55 @@ __device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs&
             const int src = __ffs(ball) - 1;
             const int dig = __shfl_sync(0xffffffffu, found, src);
             const unsigned ab = __shfl_sync(0xffffffffu, above, src);
+            const unsigned ib = __shfl_sync(0xffffffffu, inbin, src);
             if (lane == 0) {
                 ctl[0] = dig;
                 ctl[2] = remaining - (int)ab;
+                // keys already above (Kt - remaining) + this pass's keys above and in the digit
+                ctl[4] = (Kt - remaining) + (int)(ab + ib) <= kEmsCand;
             }
         }
         __syncthreads();
         prefix |= (U)ctl[0] << shift;
         pmask |= (U)255 << shift;
         remaining = ctl[2];
+        stop = ctl[4];
         __syncthreads();
+        if (stop) break;
     }
-    // ---- keep the keys above the threshold and the first `remaining` keys equal to it
-    if (tid == 0) ctl[3] = 0;
-    int eq = 0;
+    // ---- keep: everything at or above the prefix (early exit), or above T plus the first
+    // `remaining` keys equal to T in candidate order (full depth)
+    if (stop) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) eq += (tid * R + r < J && u[r] == prefix && Kt > 0);
-    int incl = eq;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int rank = incl - eq;   // equal keys before this thread, in candidate order
-    for (int w = 0; w < warp; ++w) rank += wsum[w];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int j = tid * R + r;
-        if (j < J && Kt > 0) {
-            bool take = u[r] > prefix;
-            if (u[r] == prefix) take = rank++ < remaining;
-            if (take) {
-                int m, n;
-                ems_mode_of(j, lim, row, dc, m, n);
+        for (int r = 0; r < R; ++r) {
+            if (tid * R + r < J && (u[r] & pmask) >= prefix) {
                 const int slot = atomicAdd(&ctl[3], 1);
-                keep[slot] = EmsKey{(unsigned long long)u[r], ~(unsigned)((n + half) * P + (m + half)), 0u};
+                keep[slot] = EmsKey{(unsigned long long)u[r], ~(unsigned)pj[r], 0u};
+            }
+        }
+    } else if (Kt > 0) {
+        int eq = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) eq += (tid * R + r < J && u[r] == prefix);
+        int incl = eq;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        int rank = incl - eq;   // equal keys before this thread, in candidate order
+        for (int w = 0; w < warp; ++w) rank += wsum[w];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (tid * R + r < J) {
+                bool take = u[r] > prefix;
+                if (u[r] == prefix) take = rank++ < remaining;
+                if (take) {
+                    const int slot = atomicAdd(&ctl[3], 1);
+                    keep[slot] = EmsKey{(unsigned long long)u[r], ~(unsigned)pj[r], 0u};
+                }
             }
         }
     }
@@ -299,19 +326,43 @@ __device__ void ems_rank_block(const Spec& spec, int P, int cell, const EmsArgs&
         wsum[nwarps + warp] = npos;
     }
     __syncthreads();
-    // ---- warp 0: order the survivors (rank = number of better keys) and write the scratch
-    if (warp == 0) {
-        const int L = ctl[3];
+    // ---- rank the survivors over the whole block: thread t compares candidate t / 8 with the
+    // eighth (t % 8) of the others, eight lanes sum the partial ranks; keep the first Kt
+    {
+        const int C = ctl[3];
         EmsKey* dst = out.keys + (size_t)cell * kEmsMaxK;
-        for (int i = lane; i < L; i += 32) {
-            const EmsKey ki = keep[i];
-            int rk = 0;
-            for (int k = 0; k < L; ++k) rk += key_better(keep[k], ki);
-            dst[rk] = ki;
+        const int i = tid >> 3, part = tid & 7;
+        int rk = 0;
+        EmsKey ki{0ull, 0u, 0u};
+        if (i < C) {
+            ki = keep[i];
+            for (int k = part; k < C; k += 8) rk += key_better(keep[k], ki);
         }
+        rk += __shfl_xor_sync(0xffffffffu, rk, 1);
+        rk += __shfl_xor_sync(0xffffffffu, rk, 2);
+        rk += __shfl_xor_sync(0xffffffffu, rk, 4);
+        if (i < C && part == 0 && rk < Kt) dst[rk] = ki;
+        // blocks narrower than 512 threads: further rounds (uniform trip count, so every lane
+        // takes part in the shuffles)
+        for (int base = nt / 8; base < C; base += nt / 8) {
+            const int ii = base + i;
+            EmsKey kj{0ull, 0u, 0u};
+            int r2 = 0;
+            if (ii < C) {
+                kj = keep[ii];
+                for (int k = part; k < C; k += 8) r2 += key_better(keep[k], kj);
+            }
+            r2 += __shfl_xor_sync(0xffffffffu, r2, 1);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, 2);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, 4);
+            if (ii < C && part == 0 && r2 < Kt) dst[r2] = kj;
+        }
+    }
+    if (warp == 0) {
+        const int C = ctl[3];
         if (lane == 0) {
             EmsCellInfo inf;
-            inf.L = L;
+            inf.L = C < Kt ? C : Kt;
             inf.J = J;
             inf.is_f64 = sizeof(T) == 8;
             int np = 0;
