@@ -282,7 +282,18 @@ template <int NT>
 __device__ __forceinline__ float cell_abs_sum(const float* __restrict__ h, const float* __restrict__ w, int64_t q0,
                                               int64_t q1, float inv_area, float* red) {
     float s = 0.0f;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += NT) {
+    int64_t q = q0 + threadIdx.x;
+    for (; q + 3 * NT < q1; q += 4 * NT) {   // four independent sample pairs in flight
+        float hv[4], wv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { hv[k] = h[q + k * NT]; wv[k] = w[q + k * NT]; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float v = fabsf(wv[k] * hv[k]);
+            s += (v <= 3.0e38f) ? v : 0.0f;
+        }
+    }
+    for (; q < q1; q += NT) {
         const float v = fabsf(w[q] * h[q]);
         s += (v <= 3.0e38f) ? v : 0.0f;
     }
