@@ -18,6 +18,7 @@
 #include "enufft.h"
 #include "internal.h"
 #include "kernels_misc.cuh"
+#include "large_args.cuh"
 
 using namespace enufft;
 
@@ -87,8 +88,27 @@ struct enufft_plan_s {
     int fwd_per_sm = 0, adj_per_sm = 0;
     double inv_phi[kMaxHalf + 1] = {};
     KernelPoly poly = {};
+    // large-grid (n_f = 256) route: cells in batches with bounded scratch
+    bool large = false;
+    struct LBatch {
+        int cell0, ncells, block0, nblocks;
+        int64_t p0;
+    };
+    std::vector<LBatch> lbatches;
+    int4* d_lblocks = nullptr;
+    int* d_ltile_cnt = nullptr;
+    float* d_ltile_abs = nullptr;
+    int* d_ltile_off = nullptr;
+    int* d_ltile_cur = nullptr;
+    float4* d_lrec = nullptr;
+    float* d_lgrid = nullptr;
+    int lmax_cells = 0;
     std::string err;
 };
+
+// batch bounds of the large route: records (16 B per sample) and fine grids (256 KB per cell)
+static constexpr int64_t kLargeBatchPoints = (int64_t)1 << 26;
+static constexpr int kLargeBatchCells = 512;
 
 static thread_local std::string g_last_error;
 
@@ -237,6 +257,13 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_twiddle);
     cudaFree(p->ems_scratch.keys);
     cudaFree(p->ems_scratch.info);
+    cudaFree(p->d_lblocks);
+    cudaFree(p->d_ltile_cnt);
+    cudaFree(p->d_ltile_abs);
+    cudaFree(p->d_ltile_off);
+    cudaFree(p->d_ltile_cur);
+    cudaFree(p->d_lrec);
+    cudaFree(p->d_lgrid);
     cudaSetDevice(cur);
     delete p;
     return ENUFFT_OK;
@@ -296,7 +323,12 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         enufft_plan_destroy(p);
         return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the plain FP32 per-cell path is not built");
     }
-    if (NF > 128 || !fused_supported(p->dbl, NF, W)) {
+    p->large = (NF == kLNF && !p->dbl);
+    if (p->large && (W < 4 || W > 8 || o.modes > 2 * kMaxHalfL)) {
+        enufft_plan_destroy(p);
+        return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the n_f = 256 route supports widths 4..8");
+    }
+    if (!p->large && (NF > 128 || !fused_supported(p->dbl, NF, W))) {
         enufft_plan_destroy(p);
         char buf[160];
         snprintf(buf, sizeof buf, "plan_create: no kernel for %s n_f=%d width=%d", p->dbl ? "fp64" : "fp32", NF, W);
@@ -391,6 +423,56 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         cudaMemsetAsync(p->d_offsets, 0, sizeof(int64_t), p->stream);
         cudaStreamSynchronize(p->stream);
     }
+    if (p->large) {
+        // batches of consecutive cells with bounded record and grid scratch; bin/scatter blocks
+        std::vector<int4> blocks;
+        int64_t max_pts = 0;
+        for (int64_t c = 0; c < n_cells;) {
+            enufft_plan_s::LBatch b{(int)c, 0, (int)blocks.size(), 0, off[c]};
+            while (c < n_cells && b.ncells < kLargeBatchCells &&
+                   (b.ncells == 0 || off[c + 1] - b.p0 <= kLargeBatchPoints)) {
+                for (int64_t q = off[c]; q < off[c + 1]; q += kLBinBlock)
+                    blocks.push_back(make_int4(b.ncells, (int)(q - b.p0), (int)std::min<int64_t>(off[c + 1] - b.p0, q - b.p0 + kLBinBlock), 0));
+                ++b.ncells;
+                ++c;
+            }
+            b.nblocks = (int)blocks.size() - b.block0;
+            max_pts = std::max<int64_t>(max_pts, off[c] - b.p0);
+            p->lmax_cells = std::max(p->lmax_cells, b.ncells);
+            p->lbatches.push_back(b);
+        }
+        if (max_pts > 0x7fffffff) {
+            enufft_plan_destroy(p);
+            return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: a cell has more than 2^31 samples");
+        }
+        const size_t mc = std::max(1, p->lmax_cells);
+        if ((e = cudaMalloc(&p->d_lblocks, sizeof(int4) * std::max<size_t>(blocks.size(), 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_ltile_cnt, sizeof(int) * kLTiles * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_ltile_abs, sizeof(float) * kLTiles * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_ltile_off, sizeof(int) * (kLTiles + 1) * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_ltile_cur, sizeof(int) * kLTiles * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lgrid, sizeof(float) * kLNF * kLNF * mc)) != cudaSuccess) {
+            enufft_status st = cuda_fail(nullptr, e, "plan_create: large-route scratch");
+            enufft_plan_destroy(p);
+            return st;
+        }
+        if (!blocks.empty() && (e = cudaMemcpyAsync(p->d_lblocks, blocks.data(), sizeof(int4) * blocks.size(),
+                                                    cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) {
+            enufft_status st = cuda_fail(nullptr, e, "plan_create: block table");
+            enufft_plan_destroy(p);
+            return st;
+        }
+        cudaStreamSynchronize(p->stream);
+        if ((e = large_prepare(p->P)) != cudaSuccess) {
+            enufft_status st = cuda_fail(nullptr, e, "plan_create: large-route kernel attributes");
+            enufft_plan_destroy(p);
+            return st;
+        }
+        p->n_fused = 0;
+        *out = p;
+        return ENUFFT_OK;
+    }
     e = fused_prepare(p->dbl, NF, W, &p->fwd_per_sm, &p->adj_per_sm);
     if (e != cudaSuccess || p->fwd_per_sm < 1 || p->adj_per_sm < 1) {
         enufft_status st = e != cudaSuccess ? cuda_fail(nullptr, e, "plan_create: kernel attributes")
@@ -413,7 +495,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->n_points = p->n_points;
     info->cells_fused = p->n_fused;
     info->cells_tensor = 0;
-    info->cells_large = 0;
+    info->cells_large = p->large ? p->n_cells : 0;
     info->precision = (int)p->opts.prec;
     return ENUFFT_OK;
 }
@@ -477,9 +559,58 @@ static EmsArgs make_ems(const enufft_ems_params* prm, const double* W, int per_c
     return a;
 }
 
+static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
+                                     void* coeffs, const EmsArgs* ems) {
+    LargeArgs la;
+    memset(&la, 0, sizeof(la));
+    la.x = (const float*)x;
+    la.y = (const float*)y;
+    la.h = (const float*)h;
+    la.w = (const float*)w;
+    la.offsets = p->d_offsets;
+    la.cells = p->d_cells;
+    la.tile_cnt = p->d_ltile_cnt;
+    la.tile_abs = p->d_ltile_abs;
+    la.tile_off = p->d_ltile_off;
+    la.tile_cur = p->d_ltile_cur;
+    la.rec = p->d_lrec;
+    la.grid = p->d_lgrid;
+    la.status = p->d_ctr + 2;
+    la.poly = p->poly;
+    LargeFftArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.grid = p->d_lgrid;
+    fa.P = p->P;
+    fa.coeffs = (float*)coeffs;
+    fa.twiddle = (const cplx<float>*)p->d_twiddle;
+    for (int k = 0; k <= p->P / 2; ++k) fa.inv_phi[k] = (float)p->inv_phi[k];
+    fa.do_ems = ems ? 1 : 0;
+    if (ems) fa.ems = *ems;
+    fa.ems_out = p->ems_scratch;
+    for (const auto& b : p->lbatches) {
+        la.cell0 = fa.cell0 = b.cell0;
+        la.ncells = fa.ncells = b.ncells;
+        la.p0 = b.p0;
+        la.blocks = p->d_lblocks + b.block0;
+        cudaError_t e = cudaMemsetAsync(p->d_ltile_cnt, 0, sizeof(int) * kLTiles * b.ncells, p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ltile_abs, 0, sizeof(float) * kLTiles * b.ncells, p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(float) * kLNF * kLNF * (size_t)b.ncells, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): memset");
+        e = large_run_batch(la, std::max(b.nblocks, 0), fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): launch");
+    }
+    if (ems) {
+        ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, *ems, p->ems_scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1_ems (large): finish launch");
+    }
+    return ENUFFT_OK;
+}
+
 template <typename T>
 static enufft_status run_type1(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
                                void* coeffs, const EmsArgs* ems) {
+    if (p->large) return run_type1_large(p, x, y, h, w, coeffs, ems);
     FwdArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.x = (const T*)x;
@@ -641,6 +772,7 @@ extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad
     if (!d_grad_coeffs || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
         return fail(p, ENUFFT_ERR_ARG, "type1_backward: NULL data pointer");
     if (!aligned16(d_grad_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_backward: grad_coeffs must be 16-byte aligned");
+    if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for n_f = 256 plans");
     cudaSetDevice(p->device);
     return p->dbl ? run_adjoint<double>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w)
                   : run_adjoint<float>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w);

@@ -23,6 +23,14 @@ cudaError_t launch_type1(const FwdArgs<double>& a, int nf, int w, int grid, cuda
 cudaError_t launch_adjoint(const AdjArgs<float>& a, int nf, int w, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cudaStream_t s);
 
+// Large-grid (n_f = 256) pipeline, see large.cuh.
+struct LargeArgs;
+struct LargeFftArgs;
+cudaError_t large_prepare(int P);
+size_t large_fft_smem(int P);
+cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, const LargeFftArgs& fa, int W, int fft_grid,
+                            cudaStream_t s);
+
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).
 void set_thread_error(const std::string& msg);
 

@@ -1,0 +1,56 @@
+// large_args.cuh -- constants and kernel arguments of the large-grid (n_f = 256) pipeline.
+#pragma once
+
+#include "common.cuh"
+#include "ems.cuh"
+
+namespace enufft {
+
+constexpr int kMaxHalfL = 64;                 // P/2 <= 64
+constexpr int kLNF = 256;                     // fine grid
+constexpr int kLT = 32;                       // tile side (nodes)
+constexpr int kLTiles = (kLNF / kLT) * (kLNF / kLT);   // 64 tiles per cell
+constexpr int kLBinBlock = 4096;              // samples per bin/scatter block
+
+struct LargeArgs {
+    const float* __restrict__ x;
+    const float* __restrict__ y;
+    const float* __restrict__ h;
+    const float* __restrict__ w;
+    const int64_t* __restrict__ offsets;      // all cells (CSR)
+    const CellConst* __restrict__ cells;
+    // batch
+    int cell0, ncells;                        // cells [cell0, cell0 + ncells)
+    int64_t p0;                               // offsets[cell0]
+    const int4* __restrict__ blocks;          // bin/scatter blocks: {cell - cell0, q_begin - p0, q_end - p0, 0}
+    int* tile_cnt;                            // [ncells][64]
+    float* tile_abs;                          // [ncells][64]
+    int* tile_off;                            // [ncells][65] (record offsets, batch relative)
+    int* tile_cur;                            // [ncells][64] (scatter cursors)
+    float4* rec;                              // [batch points] tile-sorted records
+    float* grid;                              // [ncells][256][256] binary32 fine grids
+    unsigned* status;
+    KernelPoly poly;
+};
+
+constexpr int kLFftThreads = 512;
+constexpr int kLRowStride = 272;              // >= 16 * 17 (team workspace), floats
+constexpr int kLRowPairs = 32;                // row pairs per round
+
+struct LargeFftArgs {
+    const float* __restrict__ grid;           // batch fine grids
+    int cell0, ncells, P;
+    float* __restrict__ coeffs;               // all cells
+    const cplx<float>* __restrict__ twiddle;  // W_256^j
+    float inv_phi[kMaxHalfL + 1];
+    int do_ems;
+    EmsArgs ems;
+    EmsScratch ems_out;
+};
+
+__host__ __device__ constexpr size_t large_fft_smem_bytes(int P) {
+    return sizeof(cplx<float>) * (size_t)kLNF * (P / 2 + 1) + sizeof(float) * (size_t)2 * kLRowPairs * kLRowStride +
+           sizeof(cplx<float>) * kLNF + sizeof(float) * (kMaxHalfL + 1) + 64;
+}
+
+}  // namespace enufft

@@ -267,3 +267,48 @@ def test_full_size_sampled_parity_tri20480():
     assert err.max() <= 1e-5, err
     oks, osel, _, _ = oracle.ems(c[cells].cpu().numpy(), OEMS(), energy_fp32=True)
     assert np.array_equal(ks[cells].cpu().numpy(), oks) and np.array_equal(sel[cells].cpu().numpy(), osel)
+
+
+def test_large_grid_route_matches_oracle():
+    """n_f = 256 (P = 128, w = 6): the sorted-by-subgrid route (bin, scatter, tile spread, per-cell FFT)
+    against the oracle, with EMS indices bit-exact; triangles and hexagons."""
+    wl = synth.make("mixed2560_p128", seed=2, n_cells=6, q_scale=0.01)
+    g = _gpu(wl)
+    plan = enufft.Plan.for_workload(g)
+    info = plan.info()
+    assert info["fine_grid"] == 256 and info["cells_large"] == 6
+    c, ks, sel, ret = plan.type1_ems(g.x, g.y, g.h, g.w)
+    plan.sync_status()
+    cn = c.cpu().numpy()
+    err = _rel_l2(cn, oracle.type1(wl))
+    assert err.max() <= 1e-5, err
+    oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
+    assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
+    c2 = plan.type1(g.x, g.y, g.h, g.w)
+    # tile write-back adds binary32 values in a run-dependent order: reruns agree to rounding
+    assert _rel_l2(c2.cpu().numpy(), cn).max() <= 1e-6
+
+
+def test_large_grid_route_many_batches():
+    """More cells than one batch of the n_f = 256 route holds (512): sampled cells on both sides of the
+    batch boundary, plus an empty cell, against the oracle."""
+    wl = synth.make("mixed2560_p128", seed=3, n_cells=600, q_scale=0.003)
+    # make cell 5 empty
+    a, b = int(wl.offsets[5]), int(wl.offsets[6])
+    keep = torch.ones(wl.n_points, dtype=torch.bool)
+    keep[a:b] = False
+    cnt = wl.counts().clone()
+    cnt[5] = 0
+    wl.offsets = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(cnt, 0)])
+    wl.x, wl.y, wl.h, wl.w = wl.x[keep], wl.y[keep], wl.h[keep], wl.w[keep]
+    g = _gpu(wl)
+    plan = enufft.Plan.for_workload(g)
+    c = plan.type1(g.x, g.y, g.h, g.w)
+    plan.sync_status()
+    cells = [0, 5, 511, 512, 599]
+    sub = wl.cell_slice(cells)
+    ref = oracle.type1(sub)
+    got = c[cells].cpu().numpy()
+    assert np.abs(got[1]).max() == 0
+    err = _rel_l2(got, ref)
+    assert err.max() <= 1e-5, err
