@@ -255,7 +255,8 @@ def run_ours(args):
     peak, peak_src = _peaks()
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(args.workload), "peak_source": peak_src, "kernel": "type1_fused_kernel<float,128,7>",
+            "traffic": _traffic(args.workload), "peak_source": peak_src, "kernel": (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish)" if info["cells_fused"]
+                                  else "n_f = 256 route, whole step (bin, scan, scatter, tile spread, FFT, EMS finish)"),
             "algorithmic_bytes_per_launch": alg_bytes}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -304,6 +305,37 @@ def run_ours(args):
                   "ems_identical": bool(np.array_equal(oks, ks[cells].cpu().numpy()) and
                                         np.array_equal(osel, sel[cells].cpu().numpy()))}
 
+    # the plain binary32 per-cell path on the same workload (one launch sequence per cell), for the
+    # speed-up the metric states; timed the same way, fewer steps
+    plain = None
+    if not args.no_plain:
+        pplan = enufft.Plan.for_workload(wl, precision="fp32")
+        pco = pplan.new_coeffs()
+        lib.enufft_set_stream(pplan._h, ctypes.c_void_p(stream.cuda_stream))
+
+        def pstep():
+            st = lib.enufft_type1_ems(pplan._h, ptr(wl.x), ptr(wl.y), ptr(wl.h), ptr(wl.w), ptr(pco), None, 0,
+                                      ctypes.byref(pc), ptr(ks), ptr(sel), ptr(ret))
+            if st != 0:
+                raise RuntimeError(lib.enufft_last_error(pplan._h).decode())
+
+        psteps = 3
+        pstep()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(psteps):
+            pstep()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pms = _max_over_ranks(a0.elapsed_time(a1), ws) / psteps
+        pplan.sync_status()
+        plain = {"value": pts_all / (pms * 1e-3), "unit": "points/s", "ms_per_step": pms, "steps": psteps,
+                 "speedup": (pts_all / (ms * 1e-3)) / (pts_all / (pms * 1e-3)),
+                 "launches_per_step": pplan.info()["kernels_per_type1_ems"]}
+        del pplan, pco
+
     cpu_base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, cells_s, pts_s, thr, dt = _oracle_sample(lambda: wl.to("cpu"), target_s=args.ref_seconds / 4)
@@ -322,7 +354,8 @@ def run_ours(args):
                 "roofline": roof, "cpu_baseline": cpu_base,
                 "e2e": {"value": pts_all / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": 2 * args.steps,   # fused transform + EMS finish per step
+                "plain_fp32": plain,
+                "gpu_launches": info["kernels_per_type1_ems"] * args.steps,
                 "clocks": clk.summary(), "parity": parity}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -341,6 +374,7 @@ def main():
                     help="CPU seconds of the reference arm (and a quarter of it for the cpu_baseline sample)")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -195,13 +195,16 @@ enufft_status enufft_sync_status(enufft_plan plan);
 /* Human-readable text of the last error on this plan (plan == NULL: of the calling thread). */
 const char *enufft_last_error(enufft_plan plan);
 
-/* Read-only plan facts: fine grid size, effective kernel width and shape parameter, and how many
- * cells take each execution route.  Returns ENUFFT_ERR_ARG for a NULL plan or output. */
+/* Read-only plan facts: fine grid size, effective kernel width and shape parameter, how many
+ * cells take each execution route (cells_plain: the plain binary32 per-cell path of ENUFFT_FP32
+ * plans), and how many kernels one enufft_type1_ems call launches.  Returns ENUFFT_ERR_ARG for a
+ * NULL plan or output. */
 typedef struct {
     int modes, fine_grid, kernel_width;
     double beta, oversamp_effective;
     int64_t n_cells, n_points, cells_fused, cells_tensor, cells_large;
     int precision;
+    int64_t cells_plain, kernels_per_type1_ems;
 } enufft_plan_info;
 enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
 

@@ -42,7 +42,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("fine_grid", ctypes.c_int), ("kernel_width", ctypes.c_int),
                 ("beta", ctypes.c_double), ("oversamp_effective", ctypes.c_double),
                 ("n_cells", ctypes.c_int64), ("n_points", ctypes.c_int64), ("cells_fused", ctypes.c_int64),
-                ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int)]
+                ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64)]
 
 
 def load_library(path: str = LIB_PATH):

@@ -103,6 +103,11 @@ struct enufft_plan_s {
     float4* d_lrec = nullptr;
     float* d_lgrid = nullptr;
     int lmax_cells = 0;
+    // plain binary32 per-cell path
+    bool plain = false;
+    std::vector<int64_t> h_off;
+    float* d_pgrid = nullptr;
+    void* d_pbuf = nullptr;
     std::string err;
 };
 
@@ -264,6 +269,8 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_ltile_cur);
     cudaFree(p->d_lrec);
     cudaFree(p->d_lgrid);
+    cudaFree(p->d_pgrid);
+    cudaFree(p->d_pbuf);
     cudaSetDevice(cur);
     delete p;
     return ENUFFT_OK;
@@ -319,16 +326,17 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     p->sigma_eff = (double)NF / o.modes;
     // ES shape: beta = 2.30 W at sigma = 2, scaled by (1 - 1/(2 sigma)) for other sigma
     p->beta = 2.30 * W * (1.0 - 0.5 / p->sigma_eff) / 0.75;
-    if (o.prec == ENUFFT_FP32) {
+    p->plain = o.prec == ENUFFT_FP32;
+    if (p->plain && NF > 256) {
         enufft_plan_destroy(p);
-        return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the plain FP32 per-cell path is not built");
+        return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the plain FP32 path supports n_f <= 256");
     }
-    p->large = (NF == kLNF && !p->dbl);
+    p->large = (NF == kLNF && !p->dbl && !p->plain);
     if (p->large && (W < 4 || W > 8 || o.modes > 2 * kMaxHalfL)) {
         enufft_plan_destroy(p);
         return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, "plan_create: the n_f = 256 route supports widths 4..8");
     }
-    if (!p->large && (NF > 128 || !fused_supported(p->dbl, NF, W))) {
+    if (!p->large && !p->plain && (NF > 128 || !fused_supported(p->dbl, NF, W))) {
         enufft_plan_destroy(p);
         char buf[160];
         snprintf(buf, sizeof buf, "plan_create: no kernel for %s n_f=%d width=%d", p->dbl ? "fp64" : "fp32", NF, W);
@@ -423,6 +431,18 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         cudaMemsetAsync(p->d_offsets, 0, sizeof(int64_t), p->stream);
         cudaStreamSynchronize(p->stream);
     }
+    if (p->plain) {
+        p->h_off = off;
+        if ((e = cudaMalloc(&p->d_pgrid, sizeof(float) * NF * NF)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_pbuf, 2 * sizeof(float) * NF * NF)) != cudaSuccess) {
+            enufft_status st = cuda_fail(nullptr, e, "plan_create: plain-path scratch");
+            enufft_plan_destroy(p);
+            return st;
+        }
+        p->n_fused = 0;
+        *out = p;
+        return ENUFFT_OK;
+    }
     if (p->large) {
         // batches of consecutive cells with bounded record and grid scratch; bin/scatter blocks
         std::vector<int4> blocks;
@@ -497,6 +517,18 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->cells_tensor = 0;
     info->cells_large = p->large ? p->n_cells : 0;
     info->precision = (int)p->opts.prec;
+    info->cells_plain = p->plain ? p->n_cells : 0;
+    int64_t k = 0;
+    if (p->plain) {
+        for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
+        k += 2;   // EMS ranking + finish
+    } else if (p->large) {
+        for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 5 : 3) : 0;
+        k += 1;   // EMS finish
+    } else {
+        k = p->n_fused > 0 ? 2 : 0;   // fused transform + EMS finish
+    }
+    info->kernels_per_type1_ems = p->n_cells > 0 ? k : 0;
     return ENUFFT_OK;
 }
 
@@ -559,6 +591,28 @@ static EmsArgs make_ems(const enufft_ems_params* prm, const double* W, int per_c
     return a;
 }
 
+// stand-alone EMS on coefficients in global memory: ranking kernel, then the per-cell finish
+static enufft_status launch_ems(enufft_plan p, const void* d_coeffs, const EmsArgs& ea) {
+    const size_t smem = ems_smem_bytes(16, ea.k_max);
+    const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 4);
+    const int half = p->P / 2, lim = half - 1;
+    const int J = (lim > 0 ? lim * (2 * lim + 2) : 0) + 1;
+    const bool big = J > 512 * 4;   // candidates per thread of the 512-thread ranking block
+    const EmsScratch sc = p->ems_scratch;
+    if (p->dbl) {
+        if (big) ems_rank_kernel<double, 16><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
+        else ems_rank_kernel<double, 4><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
+    } else {
+        if (big) ems_rank_kernel<float, 16><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
+        else ems_rank_kernel<float, 4><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, "ems: launch");
+    ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, ea, sc);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: finish launch");
+}
+
 static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
                                      void* coeffs, const EmsArgs* ems) {
     LargeArgs la;
@@ -607,9 +661,35 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
     return ENUFFT_OK;
 }
 
+static enufft_status run_type1_plain(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
+                                     void* coeffs, const EmsArgs* ems) {
+    PlainRun r;
+    r.x = (const float*)x;
+    r.y = (const float*)y;
+    r.h = (const float*)h;
+    r.w = (const float*)w;
+    r.h_off = p->h_off.data();
+    r.n_cells = p->n_cells;
+    r.cells = p->d_cells;
+    r.NF = p->NF;
+    r.W = p->W;
+    r.P = p->P;
+    r.beta = (float)p->beta;
+    r.inv_phi = p->inv_phi;
+    r.twiddle = (const cplx<float>*)p->d_twiddle;
+    r.grid = p->d_pgrid;
+    r.buf = (cplx<float>*)p->d_pbuf;
+    r.coeffs = (cplx<float>*)coeffs;
+    r.status = p->d_ctr + 2;
+    cudaError_t e = plain_run(r, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "type1 (plain): launch");
+    return ems ? launch_ems(p, coeffs, *ems) : ENUFFT_OK;
+}
+
 template <typename T>
 static enufft_status run_type1(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
                                void* coeffs, const EmsArgs* ems) {
+    if (p->plain) return run_type1_plain(p, x, y, h, w, coeffs, ems);
     if (p->large) return run_type1_large(p, x, y, h, w, coeffs, ems);
     FwdArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -686,24 +766,7 @@ enufft_status enufft_ems(enufft_plan p, const void* d_coeffs, const double* d_mo
     if (!d_coeffs || !d_kstar || !d_sel || !d_retained) return fail(p, ENUFFT_ERR_ARG, "ems: NULL data pointer");
     cudaSetDevice(p->device);
     const EmsArgs ea = make_ems(prm, d_mode_weights, per_cell, d_kstar, d_sel, d_retained);
-    const size_t smem = ems_smem_bytes(16, prm->k_max);
-    const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 4);
-    const int half = p->P / 2, lim = half - 1;
-    const int J = (lim > 0 ? lim * (2 * lim + 2) : 0) + 1;
-    const bool big = J > 512 * 4;   // candidates per thread of the 512-thread ranking block
-    const EmsScratch sc = p->ems_scratch;
-    if (p->dbl) {
-        if (big) ems_rank_kernel<double, 16><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
-        else ems_rank_kernel<double, 4><<<grid, 512, smem, p->stream>>>((const cplx<double>*)d_coeffs, p->P, p->n_cells, ea, sc);
-    } else {
-        if (big) ems_rank_kernel<float, 16><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
-        else ems_rank_kernel<float, 4><<<grid, 512, smem, p->stream>>>((const cplx<float>*)d_coeffs, p->P, p->n_cells, ea, sc);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(p, e, "ems: launch");
-    ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, ea, sc);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: finish launch");
+    return launch_ems(p, d_coeffs, ea);
 }
 
 enufft_status enufft_ems_backward(enufft_plan p, const void* d_coeffs, const double* d_mode_weights, int per_cell,
@@ -773,6 +836,7 @@ extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad
         return fail(p, ENUFFT_ERR_ARG, "type1_backward: NULL data pointer");
     if (!aligned16(d_grad_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_backward: grad_coeffs must be 16-byte aligned");
     if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for n_f = 256 plans");
+    if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for plain FP32 plans");
     cudaSetDevice(p->device);
     return p->dbl ? run_adjoint<double>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w)
                   : run_adjoint<float>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w);

@@ -31,6 +31,23 @@ size_t large_fft_smem(int P);
 cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, const LargeFftArgs& fa, int W, int fft_grid,
                             cudaStream_t s);
 
+// Plain binary32 per-cell path (plain.cu): one launch sequence per cell.
+struct PlainRun {
+    const float *x, *y, *h, *w;
+    const int64_t* h_off;          // host copy of the CSR offsets
+    int64_t n_cells;
+    const CellConst* cells;
+    int NF, W, P;
+    float beta;
+    const double* inv_phi;         // host, P/2 + 1 entries
+    const cplx<float>* twiddle;    // device, W_NF^j
+    float* grid;                   // device scratch, NF * NF
+    cplx<float>* buf;              // device scratch, NF * NF
+    cplx<float>* coeffs;
+    unsigned* status;
+};
+cudaError_t plain_run(const PlainRun& r, cudaStream_t s);
+
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).
 void set_thread_error(const std::string& msg);
 

@@ -312,3 +312,21 @@ def test_large_grid_route_many_batches():
     assert np.abs(got[1]).max() == 0
     err = _rel_l2(got, ref)
     assert err.max() <= 1e-5, err
+
+
+@pytest.mark.parametrize("name,n,qs", [("tri20480_p64", 12, 0.3), ("hex4096_p48", 6, 0.2), ("mixed2560_p128", 3, 0.01)])
+def test_plain_fp32_path_matches_oracle(name, n, qs):
+    """The plain binary32 per-cell path (precision "fp32"): coefficients within 1e-5 of the oracle
+    and, through type1_ems, EMS indices equal to the oracle's on its own spectra."""
+    wl = synth.make(name, seed=11, n_cells=n, q_scale=qs)
+    g = _gpu(wl)
+    plan = enufft.Plan.for_workload(g, precision="fp32")
+    info = plan.info()
+    assert info["cells_fused"] == 0 and info["cells_large"] == 0
+    c, ks, sel, ret = plan.type1_ems(g.x, g.y, g.h, g.w)
+    plan.sync_status()
+    cn = c.cpu().numpy()
+    err = _rel_l2(cn, oracle.type1(wl))
+    assert err.max() <= 1e-5, err
+    oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
+    assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
