@@ -82,6 +82,7 @@ struct enufft_plan_s {
     int64_t* d_offsets = nullptr;
     int* d_order = nullptr;          // all cells, largest first
     int n_fused = 0;
+    int n_tc = 0;                    // cells d_order[n_fused ..) take the tensor-core direct sum
     unsigned* d_ctr = nullptr;       // [0] forward ticket, [1] adjoint ticket, [2] status
     EmsScratch ems_scratch = {nullptr, nullptr};   // stage-1 EMS results per cell
     void* d_twiddle = nullptr;
@@ -411,6 +412,16 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
     p->n_fused = (int)n_cells;
+    if (o.tc_max_points > 0) {
+        if (p->dbl || p->plain || p->large || p->P > 64) {
+            enufft_plan_destroy(p);
+            return fail(nullptr, ENUFFT_ERR_UNSUPPORTED,
+                        "plan_create: the tensor-core route needs a mixed-precision plan with modes <= 64");
+        }
+        for (int64_t j = 0; j < n_cells; ++j)
+            if (off[j + 1] - off[j] <= o.tc_max_points) ++p->n_tc;
+        p->n_fused = (int)(n_cells - p->n_tc);
+    }
     if (n_cells > 0) {
         e = cudaMemcpyAsync(p->d_order, order.data(), sizeof(int) * n_cells, cudaMemcpyHostToDevice, p->stream);
         if (e == cudaSuccess)
@@ -493,6 +504,11 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         *out = p;
         return ENUFFT_OK;
     }
+    if (p->n_tc > 0 && (e = tc_prepare()) != cudaSuccess) {
+        enufft_status st = cuda_fail(nullptr, e, "plan_create: tensor-core kernel attributes");
+        enufft_plan_destroy(p);
+        return st;
+    }
     e = fused_prepare(p->dbl, NF, W, &p->fwd_per_sm, &p->adj_per_sm);
     if (e != cudaSuccess || p->fwd_per_sm < 1 || p->adj_per_sm < 1) {
         enufft_status st = e != cudaSuccess ? cuda_fail(nullptr, e, "plan_create: kernel attributes")
@@ -514,7 +530,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->n_cells = p->n_cells;
     info->n_points = p->n_points;
     info->cells_fused = p->n_fused;
-    info->cells_tensor = 0;
+    info->cells_tensor = p->n_tc;
     info->cells_large = p->large ? p->n_cells : 0;
     info->precision = (int)p->opts.prec;
     info->cells_plain = p->plain ? p->n_cells : 0;
@@ -526,7 +542,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
         for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 5 : 3) : 0;
         k += 1;   // EMS finish
     } else {
-        k = p->n_fused > 0 ? 2 : 0;   // fused transform + EMS finish
+        k = (p->n_fused > 0) + (p->n_tc > 0) + 1;   // fused transform, tensor-core direct sum, EMS finish
     }
     info->kernels_per_type1_ems = p->n_cells > 0 ? k : 0;
     return ENUFFT_OK;
@@ -712,12 +728,36 @@ static enufft_status run_type1(enufft_plan p, const void* x, const void* y, cons
     a.do_ems = ems ? 1 : 0;
     if (ems) a.ems = *ems;
     a.ems_out = p->ems_scratch;
-    if (a.n_work == 0) return ENUFFT_OK;
-    cudaError_t e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned), p->stream);
-    if (e != cudaSuccess) return cuda_fail(p, e, "type1: memset");
-    const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_per_sm * p->num_sms);
-    e = launch_type1(a, p->NF, p->W, grid, p->stream);
-    if (e != cudaSuccess) return cuda_fail(p, e, "type1: launch");
+    cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (p->n_tc > 0) {
+            TcLaunch l;
+            l.x = (const float*)x;
+            l.y = (const float*)y;
+            l.h = (const float*)h;
+            l.w = (const float*)w;
+            l.offsets = p->d_offsets;
+            l.cells = p->d_cells;
+            l.list = p->d_order + p->n_fused;
+            l.n_list = p->n_tc;
+            l.P = p->P;
+            l.NF = p->NF;
+            l.num_sms = p->num_sms;
+            l.coeffs = (cplx<float>*)coeffs;
+            l.status = p->d_ctr + 2;
+            l.ems = ems;
+            l.ems_out = p->ems_scratch;
+            e = launch_tc_nudft(l, p->stream);
+            if (e != cudaSuccess) return cuda_fail(p, e, "type1: tensor-core launch");
+        }
+    }
+    if (a.n_work > 0) {
+        e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned), p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1: memset");
+        const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_per_sm * p->num_sms);
+        e = launch_type1(a, p->NF, p->W, grid, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1: launch");
+    }
     if (ems) {
         ems_finish_kernel<<<(unsigned)((p->n_cells + 127) / 128), 128, 0, p->stream>>>(p->n_cells, *ems, p->ems_scratch);
         e = cudaGetLastError();
@@ -810,7 +850,7 @@ static enufft_status run_adjoint(enufft_plan p, const void* g, const void* x, co
     a.offsets = p->d_offsets;
     a.cells = p->d_cells;
     a.order = p->d_order;
-    a.n_work = p->n_fused;
+    a.n_work = (int)p->n_cells;   // the adjoint of every cell, whichever route made its coefficients
     a.P = p->P;
     a.ticket = p->d_ctr + 1;
     a.status = p->d_ctr + 2;

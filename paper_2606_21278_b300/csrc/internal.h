@@ -48,6 +48,21 @@ struct PlainRun {
 };
 cudaError_t plain_run(const PlainRun& r, cudaStream_t s);
 
+// Tensor-core direct NUDFT of small cells (tc_nudft.cu), P <= 64, binary32 samples.
+struct TcLaunch {
+    const float *x, *y, *h, *w;
+    const int64_t* offsets;
+    const CellConst* cells;
+    const int* list;               // device, cells routed here
+    int n_list, P, NF, num_sms;
+    cplx<float>* coeffs;
+    unsigned* status;
+    const EmsArgs* ems;            // NULL: no EMS ranking
+    EmsScratch ems_out;
+};
+cudaError_t tc_prepare();
+cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s);
+
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).
 void set_thread_error(const std::string& msg);
 

@@ -1,0 +1,109 @@
+// tc.cuh -- inline-PTX wrappers for the 5th-generation tensor cores of sm_103a (tcgen05 MMA with
+// the accumulator in tensor memory), mbarriers with bounded waits, and the shared-memory operand
+// layout used by the direct-NUDFT kernel.
+#pragma once
+
+#include <stdint.h>
+
+namespace enufft {
+namespace tc {
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// ---- tensor memory: allocation by one full warp; the base address is written to shared memory
+__device__ __forceinline__ void tmem_alloc(unsigned dst_smem, unsigned ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// ---- ordering of tensor-core operations around thread synchronisation, and of generic-proxy
+// shared-memory writes before the tensor core reads them
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---- mbarriers
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase with the given parity to complete, at most `limit` polls (each try_wait
+// itself suspends for a bounded, hardware-chosen time).  Returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i)
+        if (mbar_test(addr, parity)) return true;
+    return false;
+}
+
+// ---- descriptors
+// Shared-memory matrix descriptor, no swizzling: start address, leading-dimension byte offset
+// (between core matrices adjacent along K), stride byte offset (between core matrices adjacent
+// along M or N); bit 46 is the fixed descriptor version of tcgen05.
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: binary32 accumulator, f16 A and B, both MN-major
+// (transposed), N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr unsigned idesc_f16_f32_mn(int M, int N) {
+    return (1u << 4) | (1u << 15) | (1u << 16) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+// ---- MMA issue (one thread): D[tmem] (+)= A * B
+__device__ __forceinline__ void mma_f16(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// The mbarrier at `mbar` receives one arrival when every MMA issued so far by this thread is done.
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// ---- accumulator read-back: each thread of the warp gets 16 consecutive 32-bit columns of its lane
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- operand layout (MN-major, no swizzle) of one chunk of kTcChunk samples (the K dimension)
+// and 128 features (the M or N dimension): 8 x 8 core matrices of 128 B, the 16 feature blocks of
+// one sample octet contiguous (stride 128 B), sample octets 2048 B apart.  The MMA of K step s
+// (16 samples) starts at s * 4096 B with LBO = 2048 and SBO = 128.
+constexpr int kTcChunk = 64;
+constexpr int kTcFeat = 128;
+constexpr unsigned kTcLbo = 2048, kTcSbo = 128;
+constexpr unsigned kTcOperandBytes = kTcChunk * kTcFeat * 2;   // 16 KB
+__host__ __device__ constexpr unsigned tc_off(int feature, int k) {
+    return (unsigned)((k >> 3) * 2048 + (feature >> 3) * 128 + (k & 7) * 16 + (feature & 7) * 2);
+}
+
+}  // namespace tc
+}  // namespace enufft
