@@ -309,7 +309,7 @@ def run_ours(args):
     # speed-up the metric states; timed the same way, fewer steps
     plain = None
     if not args.no_plain:
-        pplan = enufft.Plan.for_workload(wl, precision="fp32")
+        pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0)
         pco = pplan.new_coeffs()
         lib.enufft_set_stream(pplan._h, ctypes.c_void_p(stream.cuda_stream))
 

@@ -97,6 +97,46 @@ __device__ __forceinline__ void tc_phasors(float th, float tl, int m0, int slot0
     }
 }
 
+// Setup of one sample (Sec. 2.1, App. A): window test, scaled weight c / max |c|, and the centred
+// coordinates u / L of both axes as binary32 hi + lo; writes slot k of a prep buffer (zeros for
+// absent, outside or non-finite samples; the latter also latch ST_NONFINITE).
+__device__ __forceinline__ void tc_prep_sample(const FastFrame& ff, const CellConst& cc, bool present, float px,
+                                               float py, float hv, float wv, float inv_cm, float inv_nf, float* pr,
+                                               int k, unsigned* status) {
+    float c = 0.0f, txh = 0.0f, txl = 0.0f, tyh = 0.0f, tyl = 0.0f;
+    if (present) {
+        if (!(isfinite(px) && isfinite(py))) {
+            atomicOr(status, ST_NONFINITE);
+        } else {
+            float uxh, uxl, uyh, uyl;
+            two_diff(px, ff.cxh, uxh, uxl);
+            uxl = __fsub_rn(uxl, ff.cxl);
+            two_diff(py, ff.cyh, uyh, uyl);
+            uyl = __fsub_rn(uyl, ff.cyl);
+            int win = window_f32(ff, cc.edge, uxh + uxl, uyh + uyl);
+            if (win < 0) win = window_f64(cc, (double)px, (double)py);
+            if (win) {
+                const float cv = wv * hv * ff.inv_area;
+                if (!isfinite(cv)) {
+                    atomicOr(status, ST_NONFINITE);
+                } else {
+                    c = cv * inv_cm;
+                    const float qx = uxh * ff.sch, qy = uyh * ff.sch;
+                    txh = qx * inv_nf;
+                    txl = (__fmaf_rn(uxh, ff.sch, -qx) + __fmaf_rn(uxh, ff.scl, uxl * ff.sch)) * inv_nf;
+                    tyh = qy * inv_nf;
+                    tyl = (__fmaf_rn(uyh, ff.sch, -qy) + __fmaf_rn(uyh, ff.scl, uyl * ff.sch)) * inv_nf;
+                }
+            }
+        }
+    }
+    pr[k] = c;
+    pr[kCh + k] = txh;
+    pr[2 * kCh + k] = txl;
+    pr[3 * kCh + k] = tyh;
+    pr[4 * kCh + k] = tyl;
+}
+
 // eight binary32 values -> binary16 hi and lo octets (16 bytes each)
 __device__ __forceinline__ void tc_split8(const float (&v)[8], uint4& hi, uint4& lo) {
     unsigned hw[4], lw[4];
@@ -201,6 +241,15 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
         const float inv_nf = 1.0f / (float)a.NF;
         for (int i = tid; i < 64 * kHS; i += kTcThreads) hs[i] = cplx<float>{0.0f, 0.0f};
 
+        if (nch > 0) {
+            if (tid < kCh) {
+                const int64_t q = q0 + tid;
+                const bool ok = q < q1;
+                tc_prep_sample(ff, cc, ok, ok ? a.x[q] : 0.0f, ok ? a.y[q] : 0.0f, ok ? a.h[q] : 0.0f,
+                               ok ? a.w[q] : 0.0f, inv_cm, inv_nf, prep + (g & 1u) * 5 * kCh, tid, a.status);
+            }
+            __syncthreads();
+        }
         for (int ch = 0; ch < nch; ++ch, ++g) {
             const unsigned st = g & 1u, use = g >> 1;
             if (use > 0 && !tc::mbar_wait(tc::smem_addr(&mbar[st]), (use - 1) & 1u, kWaitLimit))
@@ -211,45 +260,17 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
                 tc::fence_after_sync();
                 tc_flush(tmem + 128u * ((ch / kBlockChunks) & 1), hs, warp, lane);
             }
-            float* pr = prep + st * 5 * kCh;
-            // ---- per-sample setup: window, scaled weight, centred coordinates u / L as hi + lo
-            if (tid < kCh) {
-                const int64_t q = q0 + (int64_t)ch * kCh + tid;
-                float c = 0.0f, txh = 0.0f, txl = 0.0f, tyh = 0.0f, tyl = 0.0f;
-                if (q < q1) {
-                    const float px = a.x[q], py = a.y[q];
-                    if (!(isfinite(px) && isfinite(py))) {
-                        atomicOr(a.status, ST_NONFINITE);
-                    } else {
-                        float uxh, uxl, uyh, uyl;
-                        two_diff(px, ff.cxh, uxh, uxl);
-                        uxl = __fsub_rn(uxl, ff.cxl);
-                        two_diff(py, ff.cyh, uyh, uyl);
-                        uyl = __fsub_rn(uyl, ff.cyl);
-                        int win = window_f32(ff, cc.edge, uxh + uxl, uyh + uyl);
-                        if (win < 0) win = window_f64(cc, (double)px, (double)py);
-                        if (win) {
-                            const float cv = a.w[q] * a.h[q] * ff.inv_area;
-                            if (!isfinite(cv)) {
-                                atomicOr(a.status, ST_NONFINITE);
-                            } else {
-                                c = cv * inv_cm;
-                                const float qx = uxh * ff.sch, qy = uyh * ff.sch;
-                                txh = qx * inv_nf;
-                                txl = (__fmaf_rn(uxh, ff.sch, -qx) + __fmaf_rn(uxh, ff.scl, uxl * ff.sch)) * inv_nf;
-                                tyh = qy * inv_nf;
-                                tyl = (__fmaf_rn(uyh, ff.sch, -qy) + __fmaf_rn(uyh, ff.scl, uyl * ff.sch)) * inv_nf;
-                            }
-                        }
-                    }
-                }
-                pr[tid] = c;
-                pr[kCh + tid] = txh;
-                pr[2 * kCh + tid] = txl;
-                pr[3 * kCh + tid] = tyh;
-                pr[4 * kCh + tid] = tyl;
+            const float* pr = prep + st * 5 * kCh;
+            // the raw samples of the next chunk are loaded now and set up after this chunk's operands
+            const int64_t qn = q0 + (int64_t)(ch + 1) * kCh + tid;
+            const bool load_next = tid < kCh && ch + 1 < nch && qn < q1;
+            float nx = 0.0f, ny = 0.0f, nh = 0.0f, nw = 0.0f;
+            if (load_next) {
+                nx = a.x[qn];
+                ny = a.y[qn];
+                nh = a.h[qn];
+                nw = a.w[qn];
             }
-            __syncthreads();
             // ---- operands: task (axis, sample k, feature octet o); axis 0 -> A (y, times c), 1 -> B (x)
             unsigned char* stg = smem + st * kStageBytes;
 #pragma unroll
@@ -276,6 +297,8 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
                 *reinterpret_cast<uint4*>(hi + tc::tc_off(64 + 8 * o, k)) = ih;
                 *reinterpret_cast<uint4*>(lo + tc::tc_off(64 + 8 * o, k)) = il;
             }
+            if (tid < kCh && ch + 1 < nch)
+                tc_prep_sample(ff, cc, load_next, nx, ny, nh, nw, inv_cm, inv_nf, prep + (st ^ 1u) * 5 * kCh, tid, a.status);
             tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
