@@ -97,10 +97,9 @@ struct enufft_plan_s {
     };
     std::vector<LBatch> lbatches;
     int4* d_lblocks = nullptr;
-    int* d_ltile_cnt = nullptr;
-    float* d_ltile_abs = nullptr;
-    int* d_ltile_off = nullptr;
-    int* d_ltile_cur = nullptr;
+    int2* d_lcellblk = nullptr;      // per cell: {first sort block relative to its batch, count}
+    int* d_lblk_off = nullptr;       // [sort blocks of a batch][65] tile offsets
+    float* d_lblk_abs = nullptr;     // [sort blocks of a batch][64] per-tile |c| sums
     float4* d_lrec = nullptr;
     float* d_lgrid = nullptr;
     int lmax_cells = 0;
@@ -264,10 +263,9 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->ems_scratch.keys);
     cudaFree(p->ems_scratch.info);
     cudaFree(p->d_lblocks);
-    cudaFree(p->d_ltile_cnt);
-    cudaFree(p->d_ltile_abs);
-    cudaFree(p->d_ltile_off);
-    cudaFree(p->d_ltile_cur);
+    cudaFree(p->d_lcellblk);
+    cudaFree(p->d_lblk_off);
+    cudaFree(p->d_lblk_abs);
     cudaFree(p->d_lrec);
     cudaFree(p->d_lgrid);
     cudaFree(p->d_pgrid);
@@ -457,18 +455,23 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     if (p->large) {
         // batches of consecutive cells with bounded record and grid scratch; bin/scatter blocks
         std::vector<int4> blocks;
+        std::vector<int2> cellblk(std::max<int64_t>(n_cells, 1));
         int64_t max_pts = 0;
+        int max_blocks = 0;
         for (int64_t c = 0; c < n_cells;) {
             enufft_plan_s::LBatch b{(int)c, 0, (int)blocks.size(), 0, off[c]};
             while (c < n_cells && b.ncells < kLargeBatchCells &&
                    (b.ncells == 0 || off[c + 1] - b.p0 <= kLargeBatchPoints)) {
+                const int first = (int)blocks.size() - b.block0;
                 for (int64_t q = off[c]; q < off[c + 1]; q += kLBinBlock)
                     blocks.push_back(make_int4(b.ncells, (int)(q - b.p0), (int)std::min<int64_t>(off[c + 1] - b.p0, q - b.p0 + kLBinBlock), 0));
+                cellblk[c] = make_int2(first, (int)blocks.size() - b.block0 - first);
                 ++b.ncells;
                 ++c;
             }
             b.nblocks = (int)blocks.size() - b.block0;
             max_pts = std::max<int64_t>(max_pts, off[c] - b.p0);
+            max_blocks = std::max(max_blocks, b.nblocks);
             p->lmax_cells = std::max(p->lmax_cells, b.ncells);
             p->lbatches.push_back(b);
         }
@@ -478,18 +481,19 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         }
         const size_t mc = std::max(1, p->lmax_cells);
         if ((e = cudaMalloc(&p->d_lblocks, sizeof(int4) * std::max<size_t>(blocks.size(), 1))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_ltile_cnt, sizeof(int) * kLTiles * mc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_ltile_abs, sizeof(float) * kLTiles * mc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_ltile_off, sizeof(int) * (kLTiles + 1) * mc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_ltile_cur, sizeof(int) * kLTiles * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lcellblk, sizeof(int2) * cellblk.size())) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lblk_off, sizeof(int) * (kLTiles + 1) * std::max(max_blocks, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTiles * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lgrid, sizeof(float) * kLNF * kLNF * mc)) != cudaSuccess) {
             enufft_status st = cuda_fail(nullptr, e, "plan_create: large-route scratch");
             enufft_plan_destroy(p);
             return st;
         }
-        if (!blocks.empty() && (e = cudaMemcpyAsync(p->d_lblocks, blocks.data(), sizeof(int4) * blocks.size(),
-                                                    cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) {
+        if ((!blocks.empty() && (e = cudaMemcpyAsync(p->d_lblocks, blocks.data(), sizeof(int4) * blocks.size(),
+                                                     cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(p->d_lcellblk, cellblk.data(), sizeof(int2) * cellblk.size(), cudaMemcpyHostToDevice,
+                                 p->stream)) != cudaSuccess) {
             enufft_status st = cuda_fail(nullptr, e, "plan_create: block table");
             enufft_plan_destroy(p);
             return st;
@@ -539,7 +543,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
         k += 2;   // EMS ranking + finish
     } else if (p->large) {
-        for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 5 : 3) : 0;
+        for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 3 : 2) : 0;   // sort, spread, FFT
         k += 1;   // EMS finish
     } else {
         k = (p->n_fused > 0) + (p->n_tc > 0) + 1;   // fused transform, tensor-core direct sum, EMS finish
@@ -637,12 +641,9 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
     la.y = (const float*)y;
     la.h = (const float*)h;
     la.w = (const float*)w;
-    la.offsets = p->d_offsets;
     la.cells = p->d_cells;
-    la.tile_cnt = p->d_ltile_cnt;
-    la.tile_abs = p->d_ltile_abs;
-    la.tile_off = p->d_ltile_off;
-    la.tile_cur = p->d_ltile_cur;
+    la.blk_off = p->d_lblk_off;
+    la.blk_abs = p->d_lblk_abs;
     la.rec = p->d_lrec;
     la.grid = p->d_lgrid;
     la.status = p->d_ctr + 2;
@@ -662,9 +663,8 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
         la.ncells = fa.ncells = b.ncells;
         la.p0 = b.p0;
         la.blocks = p->d_lblocks + b.block0;
-        cudaError_t e = cudaMemsetAsync(p->d_ltile_cnt, 0, sizeof(int) * kLTiles * b.ncells, p->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ltile_abs, 0, sizeof(float) * kLTiles * b.ncells, p->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(float) * kLNF * kLNF * (size_t)b.ncells, p->stream);
+        la.cell_blocks = p->d_lcellblk + b.cell0;
+        cudaError_t e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(float) * kLNF * kLNF * (size_t)b.ncells, p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): memset");
         e = large_run_batch(la, std::max(b.nblocks, 0), fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): launch");

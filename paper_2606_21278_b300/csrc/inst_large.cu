@@ -13,15 +13,13 @@ size_t large_fft_smem(int P) { return large_fft_smem_bytes(P); }
 
 template <int W>
 static void launch_spread(const LargeArgs& la, int nblocks, cudaStream_t s) {
-    large_spread_kernel<W><<<nblocks, 256, 0, s>>>(la);
+    large_spread_kernel<W><<<nblocks, kLSpreadThreads, 0, s>>>(la);
 }
 
 cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, const LargeFftArgs& fa, int W, int fft_grid,
                             cudaStream_t s) {
     if (la.ncells <= 0) return cudaSuccess;
-    if (nbin_blocks > 0) large_bin_kernel<<<nbin_blocks, 256, 0, s>>>(la);
-    large_scan_kernel<<<(la.ncells + 7) / 8, 256, 0, s>>>(la);
-    if (nbin_blocks > 0) large_scatter_kernel<<<nbin_blocks, 256, 0, s>>>(la);
+    if (nbin_blocks > 0) large_sort_kernel<<<nbin_blocks, kLSortThreads, 0, s>>>(la);
     const int nt = la.ncells * kLTiles;
     switch (W) {
         case 4: launch_spread<4>(la, nt, s); break;

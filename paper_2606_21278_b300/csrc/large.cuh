@@ -1,17 +1,16 @@
 // large.cuh -- the type-1 transform for fine grids too large for one block's shared memory
 // (n_f = 256, P up to 128): a sorted-by-subgrid pipeline over batches of cells.
 //
-//   1. bin      every sample: the 32 x 32 tile of the fine grid holding its centre node; per
-//               block, shared histograms of tile counts and of sum |w h| / |D|, then one global
-//               add per (block, tile);
-//   2. scan     per cell: tile offsets in the batch's record buffer;
-//   3. scatter  every sample into its tile's range (ranges reserved per block, slots inside a
-//               block from a shared counter) as a 16-byte record {x, y, h, w};
-//   4. spread   one block per (cell, tile): the tile's samples into a shared (32 + 2 halo)^2 tile in
-//               32-bit fixed point at the tile's own scale 2^30 (1 - 2^-8) / S_tile (S_tile bounds
-//               every node of the tile), then the tile is added to the cell's binary32 fine grid
-//               in global memory (periodic wrap) by red.global.add.f32, row by row;
-//   5. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
+//   1. sort     per block of up to 4096 consecutive samples of one cell: the 32 x 32 tile of the
+//               fine grid holding each sample's centre node, a counting sort by tile inside the
+//               block's own range of the record buffer (16-byte records {x, y, h, w}), the 65 tile
+//               offsets of the block and its per-tile sums of |w h| / |D|;
+//   2. spread   one block per (cell, tile): S_tile = the sum of the sort blocks' per-tile sums bounds
+//               every node of the tile; each warp takes the tile's segment of one sort block at a
+//               time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
+//               point at the tile's own scale 2^30 (1 - 2^-8) / S_tile; the tile is then added to the
+//               cell's binary32 fine grid in global memory (periodic wrap) by red.global.add.f32;
+//   3. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
 //               length 256), the P/2 + 1 needed columns in place, deconvolution/crop written as
 //               coalesced rows of the output, and the EMS ranking read straight from the
 //               half spectrum.
@@ -35,77 +34,86 @@ __device__ __forceinline__ int large_tile_of(const CellConst& cc, float px, floa
     return ty * (kLNF / kLT) + tx;
 }
 
-// 1. bin: counts and |c| sums per (cell, tile)
-static __global__ void __launch_bounds__(256) large_bin_kernel(const __grid_constant__ LargeArgs a) {
-    __shared__ int scnt[kLTiles];
-    __shared__ float sabs[kLTiles];
+// 1. counting sort of one block's samples by tile (per-warp histograms, then a tile-major,
+// warp-minor prefix), records written inside the block's own range
+static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_constant__ LargeArgs a) {
+    constexpr int NT = kLSortThreads, PER = kLBinBlock / NT, NW = NT / 32;
+    __shared__ int hist[NW][kLTiles];
+    __shared__ int toff[kLTiles + 1];
+    __shared__ float cabs[kLBinBlock];   // |w h| / |D| in sorted order
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int4 blk = a.blocks[blockIdx.x];
-    const int cl = blk.x, cell = a.cell0 + cl;
-    const CellConst& cc = a.cells[cell];
-    for (int i = threadIdx.x; i < kLTiles; i += blockDim.x) { scnt[i] = 0; sabs[i] = 0.f; }
+    const CellConst& cc = a.cells[a.cell0 + blk.x];
+    for (int i = tid; i < NW * kLTiles; i += NT) (&hist[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = blk.y + threadIdx.x; i < blk.z; i += blockDim.x) {
-        const int64_t q = a.p0 + i;
-        const int t = large_tile_of(cc, a.x[q], a.y[q]);
-        atomicAdd(&scnt[t], 1);
-        const float v = fabsf(a.w[q] * a.h[q]) * cc.inv_area;
-        atomicAdd(&sabs[t], (v <= 3.0e38f) ? v : 0.f);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kLTiles; i += blockDim.x) {
-        if (scnt[i]) {
-            atomicAdd(&a.tile_cnt[cl * kLTiles + i], scnt[i]);
-            atomicAdd(&a.tile_abs[cl * kLTiles + i], sabs[i]);
+    float4 s[PER];
+    int tl[PER], rk[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int v = blk.y + tid + NT * i;
+        tl[i] = -1;
+        if (v < blk.z) {
+            const int64_t q = a.p0 + v;
+            s[i] = make_float4(a.x[q], a.y[q], a.h[q], a.w[q]);
         }
     }
-}
-
-// 2. scan: per cell, tile offsets into the record buffer; cursors start at the offsets
-static __global__ void large_scan_kernel(const __grid_constant__ LargeArgs a) {
-    const int cl = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (cl >= a.ncells) return;
-    const int base = (int)(a.offsets[a.cell0 + cl] - a.p0);
-    const int c0 = a.tile_cnt[cl * kLTiles + lane], c1 = a.tile_cnt[cl * kLTiles + 32 + lane];
-    int i0 = c0, i1 = c1;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v0 = __shfl_up_sync(0xffffffffu, i0, o), v1 = __shfl_up_sync(0xffffffffu, i1, o);
-        if (lane >= o) { i0 += v0; i1 += v1; }
-    }
-    const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
-    const int e0 = base + i0 - c0, e1 = base + tot0 + i1 - c1;
-    a.tile_off[cl * (kLTiles + 1) + lane] = e0;
-    a.tile_off[cl * (kLTiles + 1) + 32 + lane] = e1;
-    a.tile_cur[cl * kLTiles + lane] = e0;
-    a.tile_cur[cl * kLTiles + 32 + lane] = e1;
-    if (lane == 31) a.tile_off[cl * (kLTiles + 1) + kLTiles] = e1 + c1;
-}
-
-// 3. scatter into tile-sorted records: each block reserves one range per tile, then fills it
-static __global__ void __launch_bounds__(256) large_scatter_kernel(const __grid_constant__ LargeArgs a) {
-    __shared__ int scnt[kLTiles];
-    __shared__ int sbase[kLTiles];
-    const int4 blk = a.blocks[blockIdx.x];
-    const int cl = blk.x, cell = a.cell0 + cl;
-    const CellConst& cc = a.cells[cell];
-    for (int i = threadIdx.x; i < kLTiles; i += blockDim.x) scnt[i] = 0;
-    __syncthreads();
-    for (int64_t i = blk.y + threadIdx.x; i < blk.z; i += blockDim.x) {
-        const int64_t q = a.p0 + i;
-        atomicAdd(&scnt[large_tile_of(cc, a.x[q], a.y[q])], 1);
+    for (int i = 0; i < PER; ++i) {
+        if (blk.y + tid + NT * i < blk.z) {
+            tl[i] = large_tile_of(cc, s[i].x, s[i].y);
+            rk[i] = atomicAdd(&hist[warp][tl[i]], 1);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kLTiles; i += blockDim.x) {
-        sbase[i] = scnt[i] ? atomicAdd(&a.tile_cur[cl * kLTiles + i], scnt[i]) : 0;
-        scnt[i] = 0;
+    if (tid < kLTiles) {   // per tile: warp bases, then the tile's count
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int c = hist[w][tid];
+            hist[w][tid] = run;
+            run += c;
+        }
+        toff[tid] = run;
     }
     __syncthreads();
-    for (int64_t i = blk.y + threadIdx.x; i < blk.z; i += blockDim.x) {
-        const int64_t q = a.p0 + i;
-        const float px = a.x[q], py = a.y[q];
-        const int t = large_tile_of(cc, px, py);
-        const int slot = sbase[t] + atomicAdd(&scnt[t], 1);
-        a.rec[slot] = make_float4(px, py, a.h[q], a.w[q]);
+    if (warp == 0) {       // exclusive scan of the 64 tile counts (two per lane)
+        const int c0 = toff[2 * lane], c1 = toff[2 * lane + 1];
+        int v = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        const int e0 = v - c0 - c1;
+        __syncwarp();
+        toff[2 * lane] = e0;
+        toff[2 * lane + 1] = e0 + c0;
+        if (lane == 31) toff[kLTiles] = v;
+        int* bo = a.blk_off + (size_t)blockIdx.x * (kLTiles + 1);
+        bo[2 * lane] = e0;
+        bo[2 * lane + 1] = e0 + c0;
+        if (lane == 31) bo[kLTiles] = v;
+    }
+    __syncthreads();
+    const float inv_area = cc.inv_area;
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+        if (tl[i] >= 0) {
+            const int slot = toff[tl[i]] + hist[warp][tl[i]] + rk[i];
+            a.rec[blk.y + slot] = s[i];
+            const float v = fabsf(s[i].w * s[i].z) * inv_area;
+            cabs[slot] = (v <= 3.0e38f) ? v : 0.0f;
+        }
+    __syncthreads();
+    {   // per-tile sums over the tile's contiguous slots, eight threads per tile
+        static_assert(NT == 8 * kLTiles, "eight threads per tile");
+        const int t = tid >> 3, sub = tid & 7;
+        float sum = 0.0f;
+        for (int i = toff[t] + sub; i < toff[t + 1]; i += 8) sum += cabs[i];
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        if (sub == 0) a.blk_abs[(size_t)blockIdx.x * kLTiles + t] = sum;
     }
 }
 
@@ -131,46 +139,68 @@ __device__ __forceinline__ void tile_taps(unsigned addr, const float (&kx)[W], c
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) large_spread_kernel(const __grid_constant__ LargeArgs a) {
+__global__ void __launch_bounds__(kLSpreadThreads) large_spread_kernel(const __grid_constant__ LargeArgs a) {
     using TC = LargeTileCfg<W>;
+    constexpr int NT = kLSpreadThreads, NW = NT / 32;
     __shared__ int tile[TC::TS * TC::TSTR];
     __shared__ CellConst scc;
+    __shared__ float fsum[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cl = blockIdx.x / kLTiles, t = blockIdx.x % kLTiles, cell = a.cell0 + cl;
     const int tx0 = (t % (kLNF / kLT)) * kLT - TC::HS, ty0 = (t / (kLNF / kLT)) * kLT - TC::HS;
     {
         const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
         int4* dst = reinterpret_cast<int4*>(&scc);
-        for (int i = threadIdx.x; i < (int)(sizeof(CellConst) / 16); i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < (int)(sizeof(CellConst) / 16); i += NT) dst[i] = src[i];
     }
-    for (int i = threadIdx.x; i < TC::TS * TC::TSTR; i += blockDim.x) tile[i] = 0;
+    for (int i = tid; i < TC::TS * TC::TSTR; i += NT) tile[i] = 0;
+    const int2 cb = a.cell_blocks[cl];
+    // S_tile: sum of the sort blocks' sums for this tile (fixed order per thread, then the warps)
+    float s = 0.0f;
+    for (int j = tid; j < cb.y; j += NT) s += a.blk_abs[(size_t)(cb.x + j) * kLTiles + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) fsum[warp] = s;
     __syncthreads();
-    const int r0 = a.tile_off[cl * (kLTiles + 1) + t], r1 = a.tile_off[cl * (kLTiles + 1) + t + 1];
-    if (r1 == r0 || !scc.valid) return;
-    const float S = a.tile_abs[cl * kLTiles + t];
+    float S = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) S += fsum[i];
+    if (!scc.valid || !(S > 0.0f)) return;   // uniform across the block: nothing to spread
     const float scale = S > 0x1p-96f ? 0x1p30f * (1.0f - 0x1p-8f) / S : 0x1p126f;
     const FastFrame ff = fast_frame(scc);
     const unsigned taddr = (unsigned)__cvta_generic_to_shared(tile);
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const float4 s = a.rec[i];
-        int nx, ny;
-        float kx[W], ky[W];
-        if (!prep_f32<kLNF, W>(ff, scc.edge, scc, a.poly, s.x, s.y, nx, ny, kx, ky, a.status)) continue;
-        const float c = s.w * s.z * ff.inv_area * scale;
-        if (!isfinite(c)) {
-            atomicOr(a.status, ST_NONFINITE);
-            continue;
+    // one sort block's segment of this tile per warp at a time; the next record is loaded before
+    // the current one is spread
+    for (int j = warp; j < cb.y; j += NW) {
+        const int b = cb.x + j;
+        const int* bo = a.blk_off + (size_t)b * (kLTiles + 1);
+        const int base = a.blocks[b].y;
+        const int r1 = base + bo[t + 1];
+        int r = base + bo[t] + lane;
+        float4 cur = r < r1 ? a.rec[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (; r < r1; r += 32) {
+            const float4 nxt = r + 32 < r1 ? a.rec[r + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            int nx, ny;
+            float kx[W], ky[W];
+            if (prep_f32<kLNF, W>(ff, scc.edge, scc, a.poly, cur.x, cur.y, nx, ny, kx, ky, a.status)) {
+                const float c = cur.w * cur.z * ff.inv_area * scale;
+                if (!isfinite(c)) {
+                    atomicOr(a.status, ST_NONFINITE);
+                } else {
+                    const int lx = nx - tx0, ly = ny - ty0;   // inside [0, TS - W] by the halo
+                    if (lx < 0 || ly < 0 || lx > TC::TS - W || ly > TC::TS - W)
+                        atomicOr(a.status, ST_BADCELL);   // cannot happen for samples sorted by this cell's frame
+                    else
+                        tile_taps<W>(taddr + 4u * (unsigned)(ly * TC::TSTR + lx), kx, ky, c);
+                }
+            }
+            cur = nxt;
         }
-        const int lx = nx - tx0, ly = ny - ty0;   // inside [0, TS - W] by the halo
-        if (lx < 0 || ly < 0 || lx > TC::TS - W || ly > TC::TS - W) {
-            atomicOr(a.status, ST_BADCELL);   // cannot happen for samples binned by this cell's frame
-            continue;
-        }
-        tile_taps<W>(taddr + 4u * (unsigned)(ly * TC::TSTR + lx), kx, ky, c);
     }
     __syncthreads();
     const float inv = 1.0f / scale;
     float* g = a.grid + (size_t)cl * kLNF * kLNF;
-    for (int i = threadIdx.x; i < TC::TS * TC::TS; i += blockDim.x) {
+    for (int i = tid; i < TC::TS * TC::TS; i += NT) {
         const int ly = i / TC::TS, lx = i % TC::TS;
         const int v = tile[ly * TC::TSTR + lx];
         if (v) atomicAdd(g + ((ty0 + ly) & (kLNF - 1)) * kLNF + ((tx0 + lx) & (kLNF - 1)), (float)v * inv);

@@ -10,24 +10,24 @@ constexpr int kMaxHalfL = 64;                 // P/2 <= 64
 constexpr int kLNF = 256;                     // fine grid
 constexpr int kLT = 32;                       // tile side (nodes)
 constexpr int kLTiles = (kLNF / kLT) * (kLNF / kLT);   // 64 tiles per cell
-constexpr int kLBinBlock = 4096;              // samples per bin/scatter block
+constexpr int kLBinBlock = 4096;              // samples per sort block (one cell's consecutive samples)
+constexpr int kLSortThreads = 512;
+constexpr int kLSpreadThreads = 256;
 
 struct LargeArgs {
     const float* __restrict__ x;
     const float* __restrict__ y;
     const float* __restrict__ h;
     const float* __restrict__ w;
-    const int64_t* __restrict__ offsets;      // all cells (CSR)
     const CellConst* __restrict__ cells;
     // batch
     int cell0, ncells;                        // cells [cell0, cell0 + ncells)
     int64_t p0;                               // offsets[cell0]
-    const int4* __restrict__ blocks;          // bin/scatter blocks: {cell - cell0, q_begin - p0, q_end - p0, 0}
-    int* tile_cnt;                            // [ncells][64]
-    float* tile_abs;                          // [ncells][64]
-    int* tile_off;                            // [ncells][65] (record offsets, batch relative)
-    int* tile_cur;                            // [ncells][64] (scatter cursors)
-    float4* rec;                              // [batch points] tile-sorted records
+    const int4* __restrict__ blocks;          // sort blocks: {cell - cell0, q_begin - p0, q_end - p0, 0}
+    const int2* __restrict__ cell_blocks;     // per batch cell: {first sort block (batch relative), count}
+    int* blk_off;                             // [sort block][kLTiles + 1]: tile offsets inside the block's range
+    float* blk_abs;                           // [sort block][kLTiles]: sum |w h| / |D| of the block's samples per tile
+    float4* rec;                              // [batch points] records {x, y, h, w}, tile-ordered per sort block
     float* grid;                              // [ncells][256][256] binary32 fine grids
     unsigned* status;
     KernelPoly poly;
