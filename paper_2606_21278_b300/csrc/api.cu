@@ -92,12 +92,13 @@ struct enufft_plan_s {
     // large-grid (n_f = 256) route: cells in batches with bounded scratch
     bool large = false;
     struct LBatch {
-        int cell0, ncells, block0, nblocks;
+        int cell0, ncells, block0, nblocks, work0, nwork;
         int64_t p0;
     };
     std::vector<LBatch> lbatches;
     int4* d_lblocks = nullptr;
     int2* d_lcellblk = nullptr;      // per cell: {first sort block relative to its batch, count}
+    int4* d_lwork = nullptr;         // spread work items of all batches (per batch: largest cells first)
     int* d_lblk_off = nullptr;       // [sort blocks of a batch][65] tile offsets
     float* d_lblk_abs = nullptr;     // [sort blocks of a batch][64] per-tile |c| sums
     float4* d_lrec = nullptr;
@@ -264,6 +265,7 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->ems_scratch.info);
     cudaFree(p->d_lblocks);
     cudaFree(p->d_lcellblk);
+    cudaFree(p->d_lwork);
     cudaFree(p->d_lblk_off);
     cudaFree(p->d_lblk_abs);
     cudaFree(p->d_lrec);
@@ -454,12 +456,12 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     }
     if (p->large) {
         // batches of consecutive cells with bounded record and grid scratch; bin/scatter blocks
-        std::vector<int4> blocks;
+        std::vector<int4> blocks, work;
         std::vector<int2> cellblk(std::max<int64_t>(n_cells, 1));
         int64_t max_pts = 0;
         int max_blocks = 0;
         for (int64_t c = 0; c < n_cells;) {
-            enufft_plan_s::LBatch b{(int)c, 0, (int)blocks.size(), 0, off[c]};
+            enufft_plan_s::LBatch b{(int)c, 0, (int)blocks.size(), 0, 0, 0, off[c]};
             while (c < n_cells && b.ncells < kLargeBatchCells &&
                    (b.ncells == 0 || off[c + 1] - b.p0 <= kLargeBatchPoints)) {
                 const int first = (int)blocks.size() - b.block0;
@@ -470,6 +472,19 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
                 ++c;
             }
             b.nblocks = (int)blocks.size() - b.block0;
+            // spread work items: cells of more than kLSplitPoints samples in parts, largest cells first
+            std::vector<int> byq(b.ncells);
+            std::iota(byq.begin(), byq.end(), 0);
+            std::stable_sort(byq.begin(), byq.end(), [&](int u, int v) {
+                return off[b.cell0 + u + 1] - off[b.cell0 + u] > off[b.cell0 + v + 1] - off[b.cell0 + v];
+            });
+            b.work0 = (int)work.size();
+            for (int u : byq) {
+                const int64_t qn = off[b.cell0 + u + 1] - off[b.cell0 + u];
+                const int parts = (int)std::max<int64_t>(1, (qn + kLSplitPoints - 1) / kLSplitPoints);
+                for (int k = 0; k < parts; ++k) work.push_back(make_int4(u, k, parts, 0));
+            }
+            b.nwork = (int)work.size() - b.work0;
             max_pts = std::max<int64_t>(max_pts, off[c] - b.p0);
             max_blocks = std::max(max_blocks, b.nblocks);
             p->lmax_cells = std::max(p->lmax_cells, b.ncells);
@@ -482,6 +497,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         const size_t mc = std::max(1, p->lmax_cells);
         if ((e = cudaMalloc(&p->d_lblocks, sizeof(int4) * std::max<size_t>(blocks.size(), 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lcellblk, sizeof(int2) * cellblk.size())) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lwork, sizeof(int4) * std::max<size_t>(work.size(), 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lblk_off, sizeof(int) * (kLTiles + 1) * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTiles * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
@@ -493,7 +509,9 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         if ((!blocks.empty() && (e = cudaMemcpyAsync(p->d_lblocks, blocks.data(), sizeof(int4) * blocks.size(),
                                                      cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) ||
             (e = cudaMemcpyAsync(p->d_lcellblk, cellblk.data(), sizeof(int2) * cellblk.size(), cudaMemcpyHostToDevice,
-                                 p->stream)) != cudaSuccess) {
+                                 p->stream)) != cudaSuccess ||
+            (!work.empty() && (e = cudaMemcpyAsync(p->d_lwork, work.data(), sizeof(int4) * work.size(),
+                                                   cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)) {
             enufft_status st = cuda_fail(nullptr, e, "plan_create: block table");
             enufft_plan_destroy(p);
             return st;
@@ -664,9 +682,10 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
         la.p0 = b.p0;
         la.blocks = p->d_lblocks + b.block0;
         la.cell_blocks = p->d_lcellblk + b.cell0;
+        la.work = p->d_lwork + b.work0;
         cudaError_t e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(float) * kLNF * kLNF * (size_t)b.ncells, p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): memset");
-        e = large_run_batch(la, std::max(b.nblocks, 0), fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
+        e = large_run_batch(la, std::max(b.nblocks, 0), b.nwork, fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): launch");
     }
     if (ems) {

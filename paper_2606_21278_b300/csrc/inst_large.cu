@@ -16,11 +16,11 @@ static void launch_spread(const LargeArgs& la, int nblocks, cudaStream_t s) {
     large_spread_kernel<W><<<nblocks, kLSpreadThreads, 0, s>>>(la);
 }
 
-cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, const LargeFftArgs& fa, int W, int fft_grid,
-                            cudaStream_t s) {
+cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
+                            int fft_grid, cudaStream_t s) {
     if (la.ncells <= 0) return cudaSuccess;
     if (nbin_blocks > 0) large_sort_kernel<<<nbin_blocks, kLSortThreads, 0, s>>>(la);
-    const int nt = la.ncells * kLTiles;
+    const int nt = nwork * kLTiles;
     switch (W) {
         case 4: launch_spread<4>(la, nt, s); break;
         case 5: launch_spread<5>(la, nt, s); break;

@@ -28,8 +28,8 @@ struct LargeArgs;
 struct LargeFftArgs;
 cudaError_t large_prepare(int P);
 size_t large_fft_smem(int P);
-cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, const LargeFftArgs& fa, int W, int fft_grid,
-                            cudaStream_t s);
+cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
+                            int fft_grid, cudaStream_t s);
 
 // Plain binary32 per-cell path (plain.cu): one launch sequence per cell.
 struct PlainRun {

@@ -5,10 +5,11 @@
 //               fine grid holding each sample's centre node, a counting sort by tile inside the
 //               block's own range of the record buffer (16-byte records {x, y, h, w}), the 65 tile
 //               offsets of the block and its per-tile sums of |w h| / |D|;
-//   2. spread   one block per (cell, tile): S_tile = the sum of the sort blocks' per-tile sums bounds
-//               every node of the tile; each warp takes the tile's segment of one sort block at a
-//               time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
-//               point at the tile's own scale 2^30 (1 - 2^-8) / S_tile; the tile is then added to the
+//   2. spread   one block per (work item, tile), a work item being a cell or, for cells of more than
+//               2^18 samples, an interleaved part of its sort blocks (work items largest cell first):
+//               S = the sum of the item's sort blocks' per-tile sums bounds every node of its tile; each
+//               warp takes the tile's segment of one sort block at a time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
+//               point at the item's own scale 2^30 (1 - 2^-8) / S; the tile is then added to the
 //               cell's binary32 fine grid in global memory (periodic wrap) by red.global.add.f32;
 //   3. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
 //               length 256), the P/2 + 1 needed columns in place, deconvolution/crop written as
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(kLSpreadThreads) large_spread_kernel(const __g
     __shared__ CellConst scc;
     __shared__ float fsum[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cl = blockIdx.x / kLTiles, t = blockIdx.x % kLTiles, cell = a.cell0 + cl;
+    const int4 wk = a.work[blockIdx.x / kLTiles];
+    const int cl = wk.x, t = blockIdx.x % kLTiles, cell = a.cell0 + cl;
     const int tx0 = (t % (kLNF / kLT)) * kLT - TC::HS, ty0 = (t / (kLNF / kLT)) * kLT - TC::HS;
     {
         const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
@@ -155,9 +157,10 @@ __global__ void __launch_bounds__(kLSpreadThreads) large_spread_kernel(const __g
     }
     for (int i = tid; i < TC::TS * TC::TSTR; i += NT) tile[i] = 0;
     const int2 cb = a.cell_blocks[cl];
-    // S_tile: sum of the sort blocks' sums for this tile (fixed order per thread, then the warps)
+    // S: the sum of this part's sort blocks' sums for this tile (fixed order per thread, then the
+    // warps) bounds every node of the part's tile
     float s = 0.0f;
-    for (int j = tid; j < cb.y; j += NT) s += a.blk_abs[(size_t)(cb.x + j) * kLTiles + t];
+    for (int j = wk.y + wk.z * tid; j < cb.y; j += wk.z * NT) s += a.blk_abs[(size_t)(cb.x + j) * kLTiles + t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) fsum[warp] = s;
@@ -169,9 +172,9 @@ __global__ void __launch_bounds__(kLSpreadThreads) large_spread_kernel(const __g
     const float scale = S > 0x1p-96f ? 0x1p30f * (1.0f - 0x1p-8f) / S : 0x1p126f;
     const FastFrame ff = fast_frame(scc);
     const unsigned taddr = (unsigned)__cvta_generic_to_shared(tile);
-    // one sort block's segment of this tile per warp at a time; the next record is loaded before
-    // the current one is spread
-    for (int j = warp; j < cb.y; j += NW) {
+    // one sort block's segment of this tile per warp at a time (this part's sort blocks: j = part
+    // mod parts); the next record is loaded before the current one is spread
+    for (int j = wk.y + wk.z * warp; j < cb.y; j += wk.z * NW) {
         const int b = cb.x + j;
         const int* bo = a.blk_off + (size_t)b * (kLTiles + 1);
         const int base = a.blocks[b].y;

@@ -13,6 +13,7 @@ constexpr int kLTiles = (kLNF / kLT) * (kLNF / kLT);   // 64 tiles per cell
 constexpr int kLBinBlock = 4096;              // samples per sort block (one cell's consecutive samples)
 constexpr int kLSortThreads = 512;
 constexpr int kLSpreadThreads = 256;
+constexpr int64_t kLSplitPoints = (int64_t)1 << 18;   // samples per spread work item (cells split above)
 
 struct LargeArgs {
     const float* __restrict__ x;
@@ -25,6 +26,7 @@ struct LargeArgs {
     int64_t p0;                               // offsets[cell0]
     const int4* __restrict__ blocks;          // sort blocks: {cell - cell0, q_begin - p0, q_end - p0, 0}
     const int2* __restrict__ cell_blocks;     // per batch cell: {first sort block (batch relative), count}
+    const int4* __restrict__ work;            // spread work items, largest cells first: {cell - cell0, part, parts, 0}
     int* blk_off;                             // [sort block][kLTiles + 1]: tile offsets inside the block's range
     float* blk_abs;                           // [sort block][kLTiles]: sum |w h| / |D| of the block's samples per tile
     float4* rec;                              // [batch points] records {x, y, h, w}, tile-ordered per sort block

@@ -330,3 +330,24 @@ def test_plain_fp32_path_matches_oracle(name, n, qs):
     assert err.max() <= 1e-5, err
     oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
     assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
+
+
+def test_full_size_sampled_parity_mixed2560():
+    """The full 2,560-cell n_f = 256 workload (1.06e9 samples) in the benchmark's launch configuration:
+    the largest cells (2e6 samples, spread in several parts), the smallest and a seeded random set,
+    checked on the central 32 x 32 modes against the oracle's sum for those modes."""
+    wl = synth.make("mixed2560_p128", seed=0, device="cuda")
+    plan = enufft.Plan.for_workload(wl)
+    c = plan.type1(wl.x, wl.y, wl.h, wl.w)
+    plan.sync_status()
+    counts = wl.counts().cpu()
+    order = torch.argsort(counts, descending=True)
+    rng = np.random.default_rng(1)
+    cells = sorted(set(order[:3].tolist() + order[-2:].tolist() + rng.choice(wl.n_cells, 3, replace=False).tolist()))
+    sub = wl.cell_slice(cells).to("cpu")
+    del wl
+    ref = oracle.type1(sub, P=32)
+    P, k = 128, 16
+    got = c[cells].cpu().numpy()[:, P // 2 - k:P // 2 + k, P // 2 - k:P // 2 + k]
+    err = _rel_l2(got, ref)
+    assert err.max() <= 1e-5, err
