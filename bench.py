@@ -115,10 +115,17 @@ def _barrier(ws):
         torch.distributed.barrier()
 
 
+def _reduce_device():
+    """Device of the scalar reductions: the GPU under NCCL, the host under gloo."""
+    if torch.distributed.is_initialized() and torch.distributed.get_backend() == "nccl":
+        return "cuda"
+    return "cpu"
+
+
 def _max_over_ranks(v, ws):
     if ws == 1:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device())
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
 
@@ -126,7 +133,7 @@ def _max_over_ranks(v, ws):
 def _sum_over_ranks(v, ws):
     if ws == 1:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device())
     torch.distributed.all_reduce(t)
     return float(t.item())
 
