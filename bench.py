@@ -158,6 +158,17 @@ def _oracle_sample(wl_cpu_fn, target_s=15.0):
     return sub.n_points / dt, sub.n_cells, sub.n_points, oracle.threads_used(), dt
 
 
+def _workload(args, seed, device):
+    """The named synthetic workload, optionally resized (--cells, --q-scale), with cells capped at
+    --max-q samples and the tensor-core routing threshold overridden by --tc-max-points."""
+    wl = synth.make(args.workload, seed=seed, device=device, n_cells=args.cells, q_scale=args.q_scale)
+    if args.max_q is not None:
+        wl = wl.truncated(args.max_q)
+    if args.tc_max_points is not None:
+        wl.tc_max_points = args.tc_max_points
+    return wl
+
+
 def run_reference(args):
     """The oracle (FP64 direct sums + EMS) on the host cores: every step is a bounded seeded sample
     of the workload's cells, sized from the warm-up so that the whole run takes about
@@ -167,7 +178,7 @@ def run_reference(args):
     if rank != 0:
         return
     oracle.lib()   # compile/load before anything is timed
-    wl = synth.make(args.workload, seed=0, n_cells=args.cells)
+    wl = _workload(args, seed=0, device="cpu")
     rng = np.random.default_rng(0)
     order = rng.permutation(wl.n_cells)
     # calibrate on a few cells (warm-up)
@@ -208,7 +219,7 @@ def run_ours(args):
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    wl = synth.make(args.workload, seed=rank, device="cuda", n_cells=args.cells)
+    wl = _workload(args, seed=rank, device="cuda")
     plan = enufft.Plan.for_workload(wl)
     info = plan.info()
     prm = enufft.EMSParams()
@@ -354,6 +365,9 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "n_cells": wl.n_cells, "n_points": wl.n_points, "modes": P,
+                           "cells_tensor_core": info["cells_tensor"], "tc_max_points": wl.tc_max_points,
+                           **({"q_scale": args.q_scale} if args.q_scale != 1.0 else {}),
+                           **({"max_q": args.max_q} if args.max_q is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
                            "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
                            "l2": f"inputs larger than L2 ({16 * wl.n_points / 1e9:.2f} GB of samples per step)",
@@ -376,6 +390,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(synth.CONFIGS))
     ap.add_argument("--cells", type=int, default=None, help="seeded subset of cells (profiling runs)")
+    ap.add_argument("--q-scale", type=float, default=1.0, help="scale of the per-cell sample counts")
+    ap.add_argument("--max-q", type=int, default=None, help="cap every cell at this many samples")
+    ap.add_argument("--tc-max-points", type=int, default=None,
+                    help="override the tensor-core routing threshold (cells with at most this many samples)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="CPU seconds of the reference arm (and a quarter of it for the cpu_baseline sample)")

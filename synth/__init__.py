@@ -66,6 +66,19 @@ class Workload:
             kw[k] = kw[k].to(device)
         return Workload(**kw)
 
+    def truncated(self, max_q: int) -> "Workload":
+        """The first min(Q, max_q) samples of every cell (a workload of bounded cell size)."""
+        cnt = self.counts()
+        keep_cnt = torch.clamp(cnt, max=max_q)
+        pos = torch.arange(self.n_points, device=self.offsets.device)
+        cell = torch.repeat_interleave(torch.arange(self.n_cells, device=cnt.device), cnt)
+        keep = (pos - self.offsets[cell]) < keep_cnt[cell]
+        new_off = torch.zeros(self.n_cells + 1, dtype=torch.int64, device=cnt.device)
+        new_off[1:] = torch.cumsum(keep_cnt, 0)
+        kw = dict(self.__dict__)
+        kw.update(offsets=new_off, x=self.x[keep], y=self.y[keep], h=self.h[keep], w=self.w[keep])
+        return Workload(**kw)
+
     def cell_slice(self, cells) -> "Workload":
         """Sub-workload holding only the listed cells (in the given order)."""
         cells = torch.as_tensor(cells, dtype=torch.int64, device=self.offsets.device)
