@@ -72,7 +72,7 @@ __device__ __forceinline__ FastFrame fast_frame(const CellConst& cc) {
 constexpr int kMaxW = 16;
 constexpr int kMaxDeg = 16;
 // monomial coefficients per kernel piece used for width W (binary32 Horner evaluation)
-__host__ __device__ constexpr int poly_deg(int W) { return W + 4 < kMaxDeg ? W + 4 : kMaxDeg; }
+__host__ __device__ constexpr int poly_deg(int W) { return W + 2 < kMaxDeg ? W + 2 : kMaxDeg; }
 struct KernelPoly {
     int w;            // kernel width (grid points)
     int deg;          // number of monomial coefficients per piece

@@ -22,6 +22,10 @@
 #include "forward.cuh"
 #include "large_args.cuh"
 
+#ifndef ENUFFT_LSPREAD_MINB
+#define ENUFFT_LSPREAD_MINB 5   // co-resident tile-spread blocks per SM the register budget is sized for
+#endif
+
 namespace enufft {
 
 // tile of a sample from a plain binary32 evaluation of its grid coordinate (only used to sort:
@@ -140,7 +144,7 @@ __device__ __forceinline__ void tile_taps(unsigned addr, const float (&kx)[W], c
 }
 
 template <int W>
-__global__ void __launch_bounds__(kLSpreadThreads) large_spread_kernel(const __grid_constant__ LargeArgs a) {
+__global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_spread_kernel(const __grid_constant__ LargeArgs a) {
     using TC = LargeTileCfg<W>;
     constexpr int NT = kLSpreadThreads, NW = NT / 32;
     __shared__ int tile[TC::TS * TC::TSTR];
