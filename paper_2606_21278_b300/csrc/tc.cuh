@@ -33,6 +33,10 @@ __device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival (release semantics at CTA scope)
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
 __device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity) {
     unsigned ok;
     asm volatile(

@@ -17,10 +17,13 @@
 // is therefore limited to 256 samples (two banks of 128 TMEM columns alternate), and finished runs
 // are added into the staged spectrum in shared memory with round-to-nearest binary32 additions.
 //
-// One CTA per cell at a time (two per SM): chunks of 32 samples are turned into operands in shared
-// memory (double buffered) by all threads while one thread issues the tcgen05 MMAs of the previous
-// chunk; the accumulator lives in tensor memory and is read back once per cell, combined through
-// shared memory, written out and ranked for EMS (Sec. 2.2).
+// One CTA per cell at a time (two per SM), warp-specialised: a control warp sets up the samples of
+// the chunk two ahead (window, scaled weight, coordinates, unit phasor steps) and issues the tcgen05
+// MMAs; eight operand warps turn each chunk of 32 samples into binary16 operands in shared memory
+// (double buffered).  The hand-offs are mbarriers with bounded waits (set-up ready, operands
+// written, MMAs done), so the operand warps never wait on a block-wide barrier inside a cell.  The
+// accumulator lives in tensor memory and is read back per run, combined through shared memory,
+// written out and ranked for EMS (Sec. 2.2).
 #include <cuda_fp16.h>
 
 #include "ems.cuh"
@@ -32,15 +35,18 @@ namespace enufft {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kFeatThreads = 256;                         // warps 0..7: operands, TMEM read-back
+constexpr int kTcThreads = kFeatThreads + 32;             // warp 8: sample set-up and MMA issue
+constexpr int kCtlWarp = kFeatThreads / 32;
 constexpr int kCh = 32;                                   // samples per chunk (K of one stage)
 constexpr unsigned kOpBytes = kCh * tc::kTcFeat * 2;      // one operand (8 KB)
 constexpr unsigned kStageBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
 constexpr int kHS = 65;                                   // row stride (complex) of the staged spectrum
 constexpr unsigned kSpecOff = 2 * kStageBytes;
 constexpr unsigned kSpecBytes = 64 * kHS * 8;
+constexpr int kPrepF = 9;                                 // per sample: c, tx hi/lo, ty hi/lo, x and y steps
 constexpr unsigned kPrepOff = kSpecOff + kSpecBytes;
-constexpr unsigned kPrepBytes = 2 * 5 * kCh * 4;          // per stage: c, tx hi/lo, ty hi/lo
+constexpr unsigned kPrepBytes = 2 * kPrepF * kCh * 4;
 constexpr unsigned kEmsOff = kPrepOff + kPrepBytes;
 constexpr unsigned kEmsBytes = (unsigned)((ems_smem_bytes(kTcThreads / 32, kEmsMaxK) + 15) / 16 * 16);
 constexpr unsigned kMiscOff = kEmsOff + kEmsBytes;
@@ -49,7 +55,7 @@ constexpr unsigned kWaitLimit = 1u << 22;
 constexpr int kBlockChunks = 8;                           // chunks accumulated per TMEM run (256 samples)
 constexpr unsigned kTmemCols = 256;                       // two 128-column accumulator banks
 static_assert(kCh % 16 == 0 && tc::tc_off(127, kCh - 1) < kOpBytes, "operand layout");
-static_assert(kTcThreads == 8 * kCh, "one (sample, feature octet) task per thread and axis");
+static_assert(kFeatThreads == 8 * kCh, "one (sample, feature octet) task per operand thread and axis");
 
 struct TcSpec {
     const cplx<float>* hs;
@@ -75,20 +81,22 @@ struct TcArgs {
     EmsScratch ems_out;
 };
 
-// e^{-2 pi i m (t + 1/2)} for m = m0 .. m0 + 7 (t = th + tl, |t| <= 1/2), zero beyond slot P
-__device__ __forceinline__ void tc_phasors(float th, float tl, int m0, int slot0, int P, float (&re)[8], float (&im)[8]) {
+// c e^{-2 pi i m (t + 1/2)} for m = m0 .. m0 + 7 (t = th + tl, |t| <= 1/2; (wr, wi) = -e^{-2 pi i t}),
+// zero beyond slot P unless FULL (P = 64).  The anchor m0 takes one fast sine/cosine of an argument
+// reduced to [-pi, pi] (absolute error below 1e-6); the 7 rotations use the accurate step.
+template <bool FULL>
+__device__ __forceinline__ void tc_phasors(float th, float tl, float wr, float wi, float c, int m0, int slot0, int P,
+                                           float (&re)[8], float (&im)[8]) {
     const float fm0 = (float)m0;
     const float p = fm0 * th;
     const float r = (p - rintf(p)) + __fmaf_rn(fm0, tl, __fmaf_rn(fm0, th, -p));
-    float s0, c0, s1, c1;
-    sincospif(2.0f * r, &s0, &c0);
-    sincospif(2.0f * (th + tl), &s1, &c1);
-    const float sg = (m0 & 1) ? -1.0f : 1.0f;
-    float zr = sg * c0, zi = -sg * s0;     // (-1)^{m0} e^{-2 pi i m0 t}
-    const float wr = -c1, wi = s1;         // step: -e^{-2 pi i t}
+    float s0, c0;
+    __sincosf(6.283185307179586f * r, &s0, &c0);
+    const float sg = (m0 & 1) ? -c : c;
+    float zr = sg * c0, zi = -sg * s0;     // c (-1)^{m0} e^{-2 pi i m0 t}
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const bool on = slot0 + j < P;
+        const bool on = FULL || slot0 + j < P;
         re[j] = on ? zr : 0.0f;
         im[j] = on ? zi : 0.0f;
         const float nr = zr * wr - zi * wi, ni = zr * wi + zi * wr;
@@ -98,8 +106,9 @@ __device__ __forceinline__ void tc_phasors(float th, float tl, int m0, int slot0
 }
 
 // Setup of one sample (Sec. 2.1, App. A): window test, scaled weight c / max |c|, and the centred
-// coordinates u / L of both axes as binary32 hi + lo; writes slot k of a prep buffer (zeros for
-// absent, outside or non-finite samples; the latter also latch ST_NONFINITE).
+// coordinates u / L of both axes as binary32 hi + lo and the unit steps -e^{-2 pi i u/L}; writes
+// slot k of a prep buffer (zeros for absent, outside or non-finite samples; the latter also latch
+// ST_NONFINITE).
 __device__ __forceinline__ void tc_prep_sample(const FastFrame& ff, const CellConst& cc, bool present, float px,
                                                float py, float hv, float wv, float inv_cm, float inv_nf, float* pr,
                                                int k, unsigned* status) {
@@ -130,11 +139,18 @@ __device__ __forceinline__ void tc_prep_sample(const FastFrame& ff, const CellCo
             }
         }
     }
+    float sx, cx, sy, cy;
+    sincospif(2.0f * (txh + txl), &sx, &cx);
+    sincospif(2.0f * (tyh + tyl), &sy, &cy);
     pr[k] = c;
     pr[kCh + k] = txh;
     pr[2 * kCh + k] = txl;
     pr[3 * kCh + k] = tyh;
     pr[4 * kCh + k] = tyl;
+    pr[5 * kCh + k] = -cx;
+    pr[6 * kCh + k] = sx;
+    pr[7 * kCh + k] = -cy;
+    pr[8 * kCh + k] = sy;
 }
 
 // eight binary32 values -> binary16 hi and lo octets (16 bytes each)
@@ -152,52 +168,50 @@ __device__ __forceinline__ void tc_split8(const float (&v)[8], uint4& hi, uint4&
     lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+__device__ __forceinline__ void feat_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFeatThreads) : "memory"); }
+
 // hs[n][m] += (D[re n][re m] - D[im n][im m], D[re n][im m] + D[im n][re m]) for one accumulator
-// bank; every thread of the block takes part (TMEM lane quarter warp & 3, column half warp >> 2)
+// bank; taken by the 256 operand threads (TMEM lane quarter warp & 3, column half warp >> 2), in
+// two passes of 16 columns
 __device__ __forceinline__ void tc_flush(unsigned bank, cplx<float>* hs, int warp, int lane) {
     const int lg = warp & 3, chh = warp >> 2;
     const int row = 32 * lg + lane;
-    const unsigned ta = bank + ((unsigned)(32 * lg) << 16) + 32 * chh;
-    float vr[32], vi[32];
-    {
-        float t0[16], t1[16], t2[16], t3[16];
-        tc::tmem_ld16(ta, t0);
-        tc::tmem_ld16(ta + 16, t1);
-        tc::tmem_ld16(ta + 64, t2);
-        tc::tmem_ld16(ta + 80, t3);
+    feat_sync();   // earlier writes of hs by other operand threads are complete
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const int c0 = 32 * chh + 16 * pass;
+        const unsigned ta = bank + ((unsigned)(32 * lg) << 16) + c0;
+        float vr[16], vi[16];
+        tc::tmem_ld16(ta, vr);
+        tc::tmem_ld16(ta + 64, vi);
         tc::tmem_ld_wait();
+        cplx<float>* dst = hs + (row & 63) * kHS + c0;
+        if (row < 64) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            vr[j] = t0[j];
-            vr[16 + j] = t1[j];
-            vi[j] = t2[j];
-            vi[16 + j] = t3[j];
+            for (int j = 0; j < 16; ++j) dst[j] = cplx<float>{dst[j].re + vr[j], dst[j].im + vi[j]};
         }
-    }
-    cplx<float>* dst = hs + (row & 63) * kHS + 32 * chh;
-    if (row < 64) {
+        feat_sync();
+        if (row >= 64) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dst[j] = cplx<float>{dst[j].re + vr[j], dst[j].im + vi[j]};
-    }
-    __syncthreads();
-    if (row >= 64) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) dst[j] = cplx<float>{dst[j].re - vi[j], dst[j].im + vr[j]};
+            for (int j = 0; j < 16; ++j) dst[j] = cplx<float>{dst[j].re - vi[j], dst[j].im + vr[j]};
+        }
+        feat_sync();
     }
     tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
 }
 
-static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_constant__ TcArgs a) {
+template <bool FULL>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tsmem[];
     unsigned char* smem = tsmem;
     cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem + kSpecOff);
     float* prep = reinterpret_cast<float*>(smem + kPrepOff);
     unsigned char* ems_sm = smem + kEmsOff;
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + kMiscOff);
-    unsigned* tbase = reinterpret_cast<unsigned*>(smem + kMiscOff + 16);
-    float* red = reinterpret_cast<float*>(smem + kMiscOff + 32);   // 8 warps
+    unsigned long long* bar_mma = reinterpret_cast<unsigned long long*>(smem + kMiscOff);   // [2] MMAs done
+    unsigned long long* bar_full = bar_mma + 2;                                              // [2] operands written
+    unsigned long long* bar_prep = bar_mma + 4;                                              // [2] set-up ready
+    unsigned* tbase = reinterpret_cast<unsigned*>(smem + kMiscOff + 48);
+    float* red = reinterpret_cast<float*>(smem + kMiscOff + 64);   // 9 warps
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = a.P, half = P / 2;
 
@@ -206,8 +220,11 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(tc::smem_addr(&mbar[0]), 1);
-        tc::mbar_init(tc::smem_addr(&mbar[1]), 1);
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(tc::smem_addr(&bar_mma[s]), 1);
+            tc::mbar_init(tc::smem_addr(&bar_full[s]), kFeatThreads);
+            tc::mbar_init(tc::smem_addr(&bar_prep[s]), 1);
+        }
         tc::mbar_init_fence();
     }
     tc::fence_before_sync();
@@ -216,7 +233,7 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
     const unsigned tmem = *tbase;
     const unsigned sbase = tc::smem_addr(smem);
     const unsigned idesc = tc::idesc_f16_f32_mn(128, 128);
-    unsigned g = 0;   // chunks issued by this CTA (stage = g & 1, use = g >> 1)
+    unsigned g = 0;   // chunks of this CTA so far (stage = g & 1, use of the stage = g >> 1)
 
     for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
         const int cell = a.list[li];
@@ -232,104 +249,117 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
             }
         for (int o = 16; o; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
         if (lane == 0) red[warp] = cm;
+        for (int i = tid; i < 64 * kHS; i += kTcThreads) hs[i] = cplx<float>{0.0f, 0.0f};
         __syncthreads();
         cm = 0.0f;
         for (int i = 0; i < kTcThreads / 32; ++i) cm = fmaxf(cm, red[i]);
         const float inv_cm = cm > 0.0f ? 1.0f / cm : 0.0f;
         const int nch = (valid && cm > 0.0f) ? (int)((q1 - q0 + kCh - 1) / kCh) : 0;
-        const FastFrame ff = fast_frame(cc);
-        const float inv_nf = 1.0f / (float)a.NF;
-        for (int i = tid; i < 64 * kHS; i += kTcThreads) hs[i] = cplx<float>{0.0f, 0.0f};
 
-        if (nch > 0) {
-            if (tid < kCh) {
-                const int64_t q = q0 + tid;
-                const bool ok = q < q1;
-                tc_prep_sample(ff, cc, ok, ok ? a.x[q] : 0.0f, ok ? a.y[q] : 0.0f, ok ? a.h[q] : 0.0f,
-                               ok ? a.w[q] : 0.0f, inv_cm, inv_nf, prep + (g & 1u) * 5 * kCh, tid, a.status);
+        if (warp == kCtlWarp) {
+            // ---- control warp: set-up two chunks ahead (loads one further ahead), MMA issue
+            const FastFrame ff = fast_frame(cc);
+            const float inv_nf = 1.0f / (float)a.NF;
+            float rx = 0.f, ry = 0.f, rh = 0.f, rw = 0.f;
+            bool rv = false;
+            auto load = [&](int ch) {
+                const int64_t q = q0 + (int64_t)ch * kCh + lane;
+                rv = ch < nch && q < q1;
+                if (rv) {
+                    rx = a.x[q];
+                    ry = a.y[q];
+                    rh = a.h[q];
+                    rw = a.w[q];
+                }
+            };
+            auto setup = [&](int ch) {   // set-up of chunk ch from the loaded samples, then signal
+                const unsigned st = (g + ch) & 1u;
+                tc_prep_sample(ff, cc, rv, rx, ry, rh, rw, inv_cm, inv_nf, prep + st * kPrepF * kCh, lane, a.status);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_prep[st]));
+            };
+            for (int ch = 0; ch < 2 && ch < nch; ++ch) {
+                load(ch);
+                setup(ch);
             }
-            __syncthreads();
-        }
-        for (int ch = 0; ch < nch; ++ch, ++g) {
-            const unsigned st = g & 1u, use = g >> 1;
-            if (use > 0 && !tc::mbar_wait(tc::smem_addr(&mbar[st]), (use - 1) & 1u, kWaitLimit))
-                atomicOr(a.status, ST_TIMEOUT);
-            if (ch >= 2 * kBlockChunks && ch % kBlockChunks == 0) {
-                // the run two blocks back is complete (the stage wait covers every earlier MMA):
-                // add it to the staged spectrum before its bank is reused
+            if (nch > 2) load(2);
+            for (int ch = 0; ch < nch; ++ch) {
+                const unsigned gc = g + ch, st = gc & 1u;
+                if (!tc::mbar_wait(tc::smem_addr(&bar_full[st]), (gc >> 1) & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
                 tc::fence_after_sync();
-                tc_flush(tmem + 128u * ((ch / kBlockChunks) & 1), hs, warp, lane);
-            }
-            const float* pr = prep + st * 5 * kCh;
-            // the raw samples of the next chunk are loaded now and set up after this chunk's operands
-            const int64_t qn = q0 + (int64_t)(ch + 1) * kCh + tid;
-            const bool load_next = tid < kCh && ch + 1 < nch && qn < q1;
-            float nx = 0.0f, ny = 0.0f, nh = 0.0f, nw = 0.0f;
-            if (load_next) {
-                nx = a.x[qn];
-                ny = a.y[qn];
-                nh = a.h[qn];
-                nw = a.w[qn];
-            }
-            // ---- operands: task (axis, sample k, feature octet o); axis 0 -> A (y, times c), 1 -> B (x)
-            unsigned char* stg = smem + st * kStageBytes;
+                if (lane == 0) {
+                    const unsigned s0 = sbase + st * kStageBytes;
+                    const unsigned acc = tmem + 128u * ((ch / kBlockChunks) & 1);
+                    const bool first = ch % kBlockChunks == 0;
 #pragma unroll
-            for (int ax = 0; ax < 2; ++ax) {
-                const int k = (lane & 7) + 8 * (warp & 3), o = (lane >> 3) + 4 * (warp >> 2);
-                const float th = pr[(ax ? 1 : 3) * kCh + k], tl = pr[(ax ? 2 : 4) * kCh + k];
-                float re[8], im[8];
-                tc_phasors(th, tl, 8 * o - half, 8 * o, P, re, im);
-                if (ax == 0) {
-                    const float c = pr[k];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        re[j] *= c;
-                        im[j] *= c;
+                    for (int s = 0; s < kCh / 16; ++s) {
+                        const uint64_t ah = tc::smem_desc(s0 + s * 4096, tc::kTcLbo, tc::kTcSbo);
+                        const uint64_t al = tc::smem_desc(s0 + kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
+                        const uint64_t bh = tc::smem_desc(s0 + 2 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
+                        const uint64_t bl = tc::smem_desc(s0 + 3 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
+                        tc::mma_f16(acc, ah, bh, idesc, (!first || s > 0) ? 1u : 0u);
+                        tc::mma_f16(acc, ah, bl, idesc, 1u);
+                        tc::mma_f16(acc, al, bh, idesc, 1u);
                     }
+                    tc::mma_commit(tc::smem_addr(&bar_mma[st]));
                 }
-                uint4 rh, rl, ih, il;
-                tc_split8(re, rh, rl);
-                tc_split8(im, ih, il);
-                unsigned char* hi = stg + (ax ? 2 : 0) * kOpBytes;
-                unsigned char* lo = hi + kOpBytes;
-                *reinterpret_cast<uint4*>(hi + tc::tc_off(8 * o, k)) = rh;
-                *reinterpret_cast<uint4*>(lo + tc::tc_off(8 * o, k)) = rl;
-                *reinterpret_cast<uint4*>(hi + tc::tc_off(64 + 8 * o, k)) = ih;
-                *reinterpret_cast<uint4*>(lo + tc::tc_off(64 + 8 * o, k)) = il;
+                __syncwarp();
+                if (ch + 2 < nch) {
+                    setup(ch + 2);   // this stage's set-up buffer was read by chunk ch, whose operands are written
+                    if (ch + 3 < nch) load(ch + 3);
+                }
             }
-            if (tid < kCh && ch + 1 < nch)
-                tc_prep_sample(ff, cc, load_next, nx, ny, nh, nw, inv_cm, inv_nf, prep + (st ^ 1u) * 5 * kCh, tid, a.status);
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const unsigned s0 = sbase + st * kStageBytes;
-                const unsigned acc = tmem + 128u * ((ch / kBlockChunks) & 1);
-                const bool first = ch % kBlockChunks == 0;
+        } else {
+            // ---- operand warps
+            const int k = (lane & 7) + 8 * (warp & 3), o = (lane >> 3) + 4 * (warp >> 2);
+            for (int ch = 0; ch < nch; ++ch) {
+                const unsigned gc = g + ch, st = gc & 1u, use = gc >> 1;
+                if (!tc::mbar_wait(tc::smem_addr(&bar_prep[st]), use & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
+                if (use > 0 && !tc::mbar_wait(tc::smem_addr(&bar_mma[st]), (use - 1) & 1u, kWaitLimit))
+                    atomicOr(a.status, ST_TIMEOUT);
+                if (ch >= 2 * kBlockChunks && ch % kBlockChunks == 0) {
+                    // the run two blocks back is complete (the stage wait covers every earlier MMA):
+                    // add it to the staged spectrum before its bank is reused
+                    tc::fence_after_sync();
+                    tc_flush(tmem + 128u * ((ch / kBlockChunks) & 1), hs, warp, lane);
+                }
+                const float* pr = prep + st * kPrepF * kCh;
+                unsigned char* stg = smem + st * kStageBytes;
 #pragma unroll
-                for (int s = 0; s < kCh / 16; ++s) {
-                    const uint64_t ah = tc::smem_desc(s0 + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                    const uint64_t al = tc::smem_desc(s0 + kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                    const uint64_t bh = tc::smem_desc(s0 + 2 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                    const uint64_t bl = tc::smem_desc(s0 + 3 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                    tc::mma_f16(acc, ah, bh, idesc, (!first || s > 0) ? 1u : 0u);
-                    tc::mma_f16(acc, ah, bl, idesc, 1u);
-                    tc::mma_f16(acc, al, bh, idesc, 1u);
+                for (int ax = 0; ax < 2; ++ax) {   // axis 0 -> A (y, times c), 1 -> B (x)
+                    const float th = pr[(ax ? 1 : 3) * kCh + k], tl = pr[(ax ? 2 : 4) * kCh + k];
+                    const float wr = pr[(ax ? 5 : 7) * kCh + k], wi = pr[(ax ? 6 : 8) * kCh + k];
+                    float re[8], im[8];
+                    tc_phasors<FULL>(th, tl, wr, wi, ax ? 1.0f : pr[k], 8 * o - half, 8 * o, P, re, im);
+                    uint4 rh, rl, ih, il;
+                    tc_split8(re, rh, rl);
+                    tc_split8(im, ih, il);
+                    unsigned char* hi = stg + (ax ? 2 : 0) * kOpBytes;
+                    unsigned char* lo = hi + kOpBytes;
+                    *reinterpret_cast<uint4*>(hi + tc::tc_off(8 * o, k)) = rh;
+                    *reinterpret_cast<uint4*>(lo + tc::tc_off(8 * o, k)) = rl;
+                    *reinterpret_cast<uint4*>(hi + tc::tc_off(64 + 8 * o, k)) = ih;
+                    *reinterpret_cast<uint4*>(lo + tc::tc_off(64 + 8 * o, k)) = il;
                 }
-                tc::mma_commit(tc::smem_addr(&mbar[st]));
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                tc::mbar_arrive(tc::smem_addr(&bar_full[st]));
+            }
+            // ---- the last one or two runs -> staged spectrum, scaled back by max |c|
+            if (nch > 0) {
+                const unsigned gl = g + nch - 1;
+                if (!tc::mbar_wait(tc::smem_addr(&bar_mma[gl & 1u]), (gl >> 1) & 1u, kWaitLimit))
+                    atomicOr(a.status, ST_TIMEOUT);
+                tc::fence_after_sync();
+                const int nb = (nch + kBlockChunks - 1) / kBlockChunks;
+                for (int b = nb >= 2 ? nb - 2 : 0; b < nb; ++b) tc_flush(tmem + 128u * (b & 1), hs, warp, lane);
+                for (int i = tid; i < 64 * kHS; i += kFeatThreads) hs[i] = cplx<float>{hs[i].re * cm, hs[i].im * cm};
             }
         }
-        // ---- epilogue: the last one or two runs -> staged spectrum, scaled back by max |c|
-        if (nch > 0) {
-            const unsigned gl = g - 1;
-            if (!tc::mbar_wait(tc::smem_addr(&mbar[gl & 1u]), (gl >> 1) & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
-            tc::fence_after_sync();
-            const int nb = (nch + kBlockChunks - 1) / kBlockChunks;
-            for (int b = nb >= 2 ? nb - 2 : 0; b < nb; ++b) tc_flush(tmem + 128u * (b & 1), hs, warp, lane);
-            for (int i = tid; i < 64 * kHS; i += kTcThreads) hs[i] = cplx<float>{hs[i].re * cm, hs[i].im * cm};
-        }
+        g += (unsigned)nch;
+        tc::fence_before_sync();
         __syncthreads();
+        tc::fence_after_sync();
         {
             float2* out = reinterpret_cast<float2*>(a.coeffs + (size_t)cell * P * P);
             for (int i = tid; i < P * P; i += kTcThreads) {
@@ -340,7 +370,7 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
         if (a.do_ems) ems_rank_block<float, 8>(TcSpec{hs, half}, P, cell, a.ems, a.ems_out, ems_sm);
         __syncthreads();
     }
-    // ---- every issued MMA has completed (each cell's epilogue waited for its last commit)
+    // ---- every issued MMA has completed (each cell's operand warps waited for its last commit)
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -348,7 +378,10 @@ static __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __
 }
 
 cudaError_t tc_prepare() {
-    return cudaFuncSetAttribute(tc_nudft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tc_nudft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_nudft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    return e;
 }
 
 cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s) {
@@ -371,7 +404,8 @@ cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s) {
     else memset(&a.ems, 0, sizeof(a.ems));
     a.ems_out = l.ems_out;
     const int grid = l.n_list < 2 * l.num_sms ? l.n_list : 2 * l.num_sms;
-    tc_nudft_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(a);
+    if (l.P == 64) tc_nudft_kernel<true><<<grid, kTcThreads, kSmemBytes, s>>>(a);
+    else tc_nudft_kernel<false><<<grid, kTcThreads, kSmemBytes, s>>>(a);
     return cudaGetLastError();
 }
 
