@@ -189,6 +189,16 @@ enufft_status enufft_ems_noalloc(int modes, int64_t n_cells, const void *d_coeff
                                  const enufft_ems_params *params, int32_t *d_kstar, int32_t *d_sel,
                                  double *d_retained_power, void *cuda_stream);
 
+/*
+ * Self-test of the failure path of the bounded device-side waits (the paper has no counterpart).
+ * Launches, on the plan's stream, one block that waits on an mbarrier nothing ever arrives at,
+ * giving up after `polls` polls exactly as the tensor-core kernel does when a hand-off never
+ * comes: the block latches the timeout bit in the plan's status word and returns, so the context
+ * stays usable.  The next enufft_sync_status then returns ENUFFT_ERR_TIMEOUT ("bounded wait
+ * expired").  polls must be in [1, 2^20]; a NULL plan or a bad count returns ENUFFT_ERR_ARG.
+ */
+enufft_status enufft_selftest_wait_timeout(enufft_plan plan, unsigned polls);
+
 /* Synchronise the plan's stream and report (then clear) any latched device-side condition. */
 enufft_status enufft_sync_status(enufft_plan plan);
 

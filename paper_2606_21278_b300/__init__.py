@@ -72,9 +72,10 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_last_error.argtypes = [vp]
     lib.enufft_last_error.restype = ctypes.c_char_p
     lib.enufft_get_plan_info.argtypes = [vp, P(_Info)]
+    lib.enufft_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint]
     for f in ("enufft_plan_create", "enufft_plan_destroy", "enufft_type1", "enufft_ems", "enufft_type1_ems",
               "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status", "enufft_set_stream",
-              "enufft_get_plan_info"):
+              "enufft_get_plan_info", "enufft_selftest_wait_timeout"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -168,6 +169,11 @@ class Plan:
         self._check(self._lib.enufft_get_plan_info(self._h, ctypes.byref(i)), "get_plan_info")
         return {f: getattr(i, f) for f, _ in _Info._fields_}
 
+    def selftest_wait_timeout(self, polls: int = 64):
+        """Latch a bounded-wait timeout on the device (see enufft_selftest_wait_timeout)."""
+        self._bind()
+        self._check(self._lib.enufft_selftest_wait_timeout(self._h, polls), "selftest_wait_timeout")
+
     def sync_status(self):
         self._check(self._lib.enufft_sync_status(self._h), "sync_status")
 
@@ -203,10 +209,12 @@ class Plan:
                                          _ptr(sel), _ptr(ret)), "ems")
         return ks, sel, ret
 
-    def type1_ems(self, x, y, h, w, params: EMSParams = EMSParams(), mode_weights=None, coeffs=None):
+    def type1_ems(self, x, y, h, w, params: EMSParams = EMSParams(), mode_weights=None, coeffs=None, out=None):
+        """Coefficients and EMS in one call; `coeffs` and `out` = (kstar, sel, retained) may be
+        preallocated (e.g. for capture in a CUDA graph)."""
         x, y, h, w = self._samples(x, y, h, w)
         coeffs = self.new_coeffs() if coeffs is None else coeffs
-        ks, sel, ret = self._ems_out(params)
+        ks, sel, ret = self._ems_out(params) if out is None else out
         mw, per = self._weights(mode_weights)
         pc = params.c()
         self._bind()

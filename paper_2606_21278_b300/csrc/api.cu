@@ -576,6 +576,14 @@ enufft_status enufft_set_stream(enufft_plan p, void* s) {
     return ENUFFT_OK;
 }
 
+enufft_status enufft_selftest_wait_timeout(enufft_plan p, unsigned polls) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "selftest_wait_timeout: NULL plan");
+    if (polls < 1 || polls > (1u << 20)) return fail(p, ENUFFT_ERR_ARG, "selftest_wait_timeout: polls must be in [1, 2^20]");
+    cudaSetDevice(p->device);
+    cudaError_t e = launch_wait_timeout(polls, p->d_ctr + 2, p->stream);
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "selftest_wait_timeout: launch");
+}
+
 enufft_status enufft_sync_status(enufft_plan p) {
     if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "sync_status: NULL plan");
     unsigned st = 0;

@@ -61,6 +61,7 @@ struct TcLaunch {
     EmsScratch ems_out;
 };
 cudaError_t tc_prepare();
+cudaError_t launch_wait_timeout(unsigned polls, unsigned* status, cudaStream_t s);
 cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s);
 
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).

@@ -377,6 +377,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// one block waiting on an mbarrier that never completes (no arrivals): the bounded wait gives up
+static __global__ void tc_wait_timeout_kernel(unsigned polls, unsigned* status) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_addr(&bar), 1);
+        tc::mbar_init_fence();
+    }
+    __syncthreads();
+    if (!tc::mbar_wait(tc::smem_addr(&bar), 0u, polls) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_wait_timeout(unsigned polls, unsigned* status, cudaStream_t s) {
+    tc_wait_timeout_kernel<<<1, 32, 0, s>>>(polls, status);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_prepare() {
     cudaError_t e = cudaFuncSetAttribute(tc_nudft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e == cudaSuccess)

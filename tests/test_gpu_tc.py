@@ -136,3 +136,18 @@ def test_tensor_core_route_rejected_where_not_built():
     g = wl.to("cuda")
     with pytest.raises(enufft.EnufftError, match="tensor-core"):
         enufft.Plan.for_workload(g, tc_max_points=100)
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
+    """A wait that nothing completes gives up after its poll limit, latches the timeout bit, and the
+    next sync reports ENUFFT_ERR_TIMEOUT; the plan then runs normally."""
+    wl = synth.make("tri81920_p64_mixed", seed=2, n_cells=6, q_scale=0.4)
+    g = wl.to("cuda")
+    plan = enufft.Plan.for_workload(g)
+    plan.selftest_wait_timeout(64)
+    with pytest.raises(enufft.EnufftError, match="status 4.*bounded wait expired"):
+        plan.sync_status()
+    plan.sync_status()   # cleared once reported
+    c = plan.type1(g.x, g.y, g.h, g.w)
+    plan.sync_status()
+    assert _rel_l2(c.cpu().numpy(), oracle.type1(wl)).max() <= 1e-5
