@@ -69,7 +69,9 @@ typedef struct {
     enufft_mask mask;     /* App. A support mask                                                 */
     double eta;           /* App. A window expansion factor: H = (eta/2) * max extent            */
     int tc_max_points;    /* cells with at most this many samples take the tensor-core direct
-                             sum (Eq. discrete_quadrature as a dense contraction); 0 = off       */
+                             sum (Eq. discrete_quadrature as a dense contraction); 0 = off.
+                             Mixed-precision plans with modes <= 64 only: other plans with a
+                             positive value return ENUFFT_ERR_UNSUPPORTED                       */
 } enufft_opts;
 
 typedef struct {

@@ -9,8 +9,6 @@ cudaError_t large_prepare(int P) {
                                 (int)large_fft_smem_bytes(P));
 }
 
-size_t large_fft_smem(int P) { return large_fft_smem_bytes(P); }
-
 template <int W>
 static void launch_spread(const LargeArgs& la, int nblocks, cudaStream_t s) {
     large_spread_kernel<W><<<nblocks, kLSpreadThreads, 0, s>>>(la);

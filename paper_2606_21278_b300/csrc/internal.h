@@ -27,7 +27,6 @@ cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cu
 struct LargeArgs;
 struct LargeFftArgs;
 cudaError_t large_prepare(int P);
-size_t large_fft_smem(int P);
 cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
                             int fft_grid, cudaStream_t s);
 

@@ -97,14 +97,12 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// ---- operand layout (MN-major, no swizzle) of one chunk of kTcChunk samples (the K dimension)
-// and 128 features (the M or N dimension): 8 x 8 core matrices of 128 B, the 16 feature blocks of
-// one sample octet contiguous (stride 128 B), sample octets 2048 B apart.  The MMA of K step s
-// (16 samples) starts at s * 4096 B with LBO = 2048 and SBO = 128.
-constexpr int kTcChunk = 64;
+// ---- operand layout (MN-major, no swizzle) of one chunk of samples (the K dimension, a multiple
+// of 16) and 128 features (the M or N dimension): 8 x 8 core matrices of 128 B, the 16 feature
+// blocks of one sample octet contiguous (stride 128 B), sample octets 2048 B apart.  The MMA of K
+// step s (16 samples) starts at s * 4096 B with LBO = 2048 and SBO = 128.
 constexpr int kTcFeat = 128;
 constexpr unsigned kTcLbo = 2048, kTcSbo = 128;
-constexpr unsigned kTcOperandBytes = kTcChunk * kTcFeat * 2;   // 16 KB
 __host__ __device__ constexpr unsigned tc_off(int feature, int k) {
     return (unsigned)((k >> 3) * 2048 + (feature >> 3) * 128 + (k & 7) * 16 + (feature & 7) * 2);
 }
