@@ -45,9 +45,11 @@ def lib():
                                           vp, vp, vp, vp, i32]
         _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, vp, vp, vp, vp]
         _lib.oracle_ems_grad_coeffs.argtypes = [i64, i32, vp, vp, i32, i32, vp, vp, vp, vp]
+        _lib.oracle_reconstruct_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp,
+                                                  vp, i32]
         for f in ("oracle_frame", "oracle_window", "oracle_type1_batch", "oracle_type1_backward_batch",
                   "oracle_ems_batch", "oracle_ems_energies", "oracle_ems_grad_coeffs",
-                  "oracle_threads_used"):
+                  "oracle_threads_used", "oracle_reconstruct_batch"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -132,6 +134,39 @@ def type1_backward(wl, G: np.ndarray, nthreads: int = 0):
                                           int(nthreads))
     assert r == 0
     return gh, gw
+
+
+def selection_mask(kstar, sel, P: int) -> np.ndarray:
+    """Mode mask [n_cells, P, P] of the selected pairs: for k < K*, pair index p = (n + P/2) P + (m + P/2)
+    marks (m, n) and its partner (-m, -n) (Sec. 2.2 selects mode pairs)."""
+    kstar = np.asarray(kstar)
+    sel = np.asarray(sel)
+    mask = np.zeros((len(kstar), P, P), dtype=np.uint8)
+    for j in range(len(kstar)):
+        for k in range(int(kstar[j])):
+            p = int(sel[j, k])
+            n, m = p // P - P // 2, p % P - P // 2
+            mask[j, n + P // 2, m + P // 2] = 1
+            mask[j, -n + P // 2, -m + P // 2] = 1
+    return mask
+
+
+def reconstruct(wl, coeffs: np.ndarray, mask: np.ndarray, nthreads: int = 0):
+    """Sec. 3.2 diagnostics for coefficients [n_cells, P, P] and a mode mask [n_cells, P, P]:
+    (hrec[n_points], stats[n_cells, 4] = eps_rel, sigma2_phys, sigma2_spec over the mask,
+    sigma2_spec over the box), see oracle_reconstruct_batch."""
+    P = wl.modes
+    off, nv, vv = _cells(wl)
+    x, y, h, w = (_f64(a) for a in (wl.x, wl.y, wl.h, wl.w))
+    c = np.ascontiguousarray(np.stack([np.asarray(coeffs).real, np.asarray(coeffs).imag], -1), dtype=np.float64)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    hrec = np.zeros(len(x))
+    stats = np.zeros((len(nv), 4))
+    r = lib().oracle_reconstruct_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w), int(P),
+                                       float(wl.eta), int(wl.mask), _p(c), _p(m), _p(hrec), _p(stats),
+                                       int(nthreads))
+    assert r == 0, "oracle_reconstruct_batch failed"
+    return hrec, stats
 
 
 def ems(coeffs: np.ndarray, params: EMSParams = EMSParams(), mode_weights=None, energy_fp32: bool = False,

@@ -16,6 +16,9 @@
  *               "alpha_c", "f_cum", "k_elastic" (+ the footnote bounding all sums by J_max)
  *   gradient    derivative of the EMS-retained power with the selected set held fixed; it is the
  *               adjoint (type-2 sum) of the quadrature above
+ *   diagnostics Sec. 3.2: the truncated series h_rec (Eq. "tri_series") over a set of modes at the
+ *               samples, the relative reconstructed RMSE (Eq. "alps_relative_rmse") and the physical
+ *               and spectral variances of Parseval's check (Eq. "spectral_variance")
  *
  * Readings where the paper is silent (documented with the build):
  *   - mode box m, n in [-P/2, P/2); EMS candidates are mode pairs +-(m,n) with |m|,|n| <= P/2-1,
@@ -272,6 +275,65 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
             grad_h[q] = w[q] * v / f.area;
             grad_w[q] = h[q] * v / f.area;
         }
+    }
+    return err ? -1 : 0;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* Sec. 3.2 diagnostics: reconstruction at the samples, relative RMSE, Parseval variances       */
+/* ----------------------------------------------------------------------------------------- */
+
+/* Exported: for every cell, with the mode set given as a mask over the P x P box:
+ *   hrec_q  = Re sum_{mu in set} h_mu e^{+i k_mu . x'_q}   (Eq. tri_series; 0 outside the window)
+ *   stats[4 j + 0] = eps_rel = sqrt(sum_q (h_q - hrec_q)^2 / sum_q h_q^2) over the windowed samples
+ *                    (Eq. alps_relative_rmse; the 1/Q factors cancel; 0 when every h_q is 0)
+ *   stats[4 j + 1] = sigma2_phys = (1/|D|) sum_q w_q h_q^2 over the windowed samples
+ *   stats[4 j + 2] = sigma2_spec over the set, (m, n) != (0, 0)
+ *   stats[4 j + 3] = sigma2_spec over the whole box, (m, n) != (0, 0)       (Eq. spectral_variance) */
+int oracle_reconstruct_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
+                             const double *verts, const double *x, const double *y, const double *h,
+                             const double *w, int P, double eta, int mask, const double *coeffs,
+                             const uint8_t *modes, double *hrec, double *stats, int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : err)
+#endif
+    for (int64_t j = 0; j < n_cells; ++j) {
+        oframe f;
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        const double *cj = coeffs + 2 * (size_t)P * P * j;
+        const uint8_t *sj = modes + (size_t)P * P * j;
+        double *G = (double *)calloc(2 * (size_t)P * P, sizeof(double));
+        if (!G) { err |= 2; continue; }
+        double spec_set = 0.0, spec_all = 0.0;
+        for (int i = 0; i < P * P; ++i) {
+            const int dc = (i == (P / 2) * P + P / 2);
+            const double e = cj[2 * i] * cj[2 * i] + cj[2 * i + 1] * cj[2 * i + 1];
+            if (!dc) spec_all += e;
+            if (sj[i]) {
+                G[2 * i] = cj[2 * i];
+                G[2 * i + 1] = cj[2 * i + 1];
+                if (!dc) spec_set += e;
+            }
+        }
+        double err2 = 0.0, h2 = 0.0, wh2 = 0.0;
+        for (int64_t q = offsets[j]; q < offsets[j + 1]; ++q) {
+            if (!in_window(&f, x[q], y[q])) {
+                hrec[q] = 0.0;
+                continue;
+            }
+            const double v = type2_point(&f, P, G, x[q], y[q]);
+            hrec[q] = v;
+            err2 += (h[q] - v) * (h[q] - v);
+            h2 += h[q] * h[q];
+            wh2 += w[q] * h[q] * h[q];
+        }
+        free(G);
+        stats[4 * j + 0] = h2 > 0.0 ? sqrt(err2 / h2) : 0.0;
+        stats[4 * j + 1] = wh2 / f.area;
+        stats[4 * j + 2] = spec_set;
+        stats[4 * j + 3] = spec_all;
     }
     return err ? -1 : 0;
 }

@@ -392,3 +392,51 @@ def test_gibbs_overshoot_matches_printed_constant():
     for m in range(-(2 * Nt + 1), 2 * Nt + 2):
         S += (c[m + P // 2] * np.exp(2j * math.pi * m * xN / L)).real
     assert abs((S - dh) / dh - _golden("gibbs_overshoot.txt")["overshoot_over_dh"]) < 2e-3
+
+
+# ----------------------------------------------------------------------------------------------
+# reconstruction diagnostics (Sec. 3.2: Eqs. tri_series, alps_relative_rmse, spectral_variance)
+# ----------------------------------------------------------------------------------------------
+
+def test_reconstruction_with_every_mode_is_the_inverse_dft():
+    """On an equidistant grid the truncated series over the full N x N box is the inverse DFT: h_rec = h
+    at every sample (eps_rel = 0), and Parseval holds exactly: sigma2_phys = sigma2_spec(box) + |h_00|^2."""
+    N = 16
+    rng = np.random.default_rng(21)
+    vals = torch.tensor(rng.standard_normal(N * N) * 300.0 + 40.0)
+    wl = synth.regular_grid_square_cell(N, lambda xp, yp: vals, half=0.6, center=(0.3, -0.2), modes=N)
+    c = oracle.type1(wl)
+    mask = np.ones((1, N, N), dtype=np.uint8)
+    hrec, st = oracle.reconstruct(wl, c, mask)
+    assert np.abs(hrec - vals.numpy()).max() < 1e-10 * np.abs(vals.numpy()).max()
+    assert st[0, 0] < 1e-12
+    dc = abs(c[0, N // 2, N // 2]) ** 2
+    assert abs(st[0, 1] - (st[0, 3] + dc)) < 1e-12 * st[0, 1]
+    assert st[0, 2] == st[0, 3]
+
+
+def test_reconstruction_of_a_plane_wave_from_its_pair():
+    """A cosine with integer wavenumbers is one mode pair; the series over that pair reproduces it at the
+    samples (eps_rel = 0) and both variances equal A^2 / 2."""
+    N, P, A, phi, ms, ns = 16, 8, 700.0, 0.4, 2, 3
+    L = 1.5
+    f = lambda xp, yp: A * torch.cos(2 * math.pi * (ms * xp + ns * yp) / L + phi)
+    wl = synth.regular_grid_square_cell(N, f, half=L / 2, modes=P)
+    c = oracle.type1(wl)
+    kstar = np.array([1])
+    sel = np.array([[(ns + P // 2) * P + (ms + P // 2)] + [-1] * 11])
+    mask = oracle.selection_mask(kstar, sel, P)
+    assert mask.sum() == 2 and mask[0, _idx(P, -ms, -ns)[0], _idx(P, -ms, -ns)[1]] == 1
+    hrec, st = oracle.reconstruct(wl, c, mask)
+    assert np.abs(hrec - wl.h.numpy()).max() < 1e-9 * A
+    assert st[0, 0] < 1e-11
+    assert abs(st[0, 1] - A * A / 2) < 1e-9 * A * A and abs(st[0, 2] - A * A / 2) < 1e-9 * A * A
+
+
+def test_reconstruction_from_no_modes():
+    """An empty mode set reconstructs zero: eps_rel = 1 and no spectral variance in the set."""
+    wl = synth.make("tri20480_p64", seed=3, n_cells=2, q_scale=0.05)
+    c = oracle.type1(wl)
+    hrec, st = oracle.reconstruct(wl, c, np.zeros((2, 64, 64), dtype=np.uint8))
+    assert np.all(hrec == 0) and np.allclose(st[:, 0], 1.0) and np.all(st[:, 2] == 0)
+    assert np.all(st[:, 3] > 0) and np.all(st[:, 1] > 0)
