@@ -166,6 +166,27 @@ enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs,
                                     const void *d_y, const void *d_h, const void *d_w, void *d_grad_h,
                                     void *d_grad_w);
 
+/*
+ * Reconstruction diagnostics of Sec. 3.2 from coefficients and an EMS selection (as written by
+ * enufft_type1_ems / enufft_ems on this plan).  The mode set is the selected pairs and their
+ * partners: for k < kstar[j], p = sel[j][k] marks (m, n) with p = (n + P/2) P + (m + P/2), and
+ * (-m, -n).  On the plan's stream, per cell j:
+ *   d_hrec[q]        h_rec(x_q) = Re sum over the set of h_mn exp(+i (k_m x'_q + k_n y'_q)), the
+ *                    truncated series of Eq. tri_series at the samples (0 outside the window;
+ *                    may be NULL); float or double as the plan's samples
+ *   d_stats[4 j + 0] eps_rel = sqrt(sum_q (h_q - h_rec(x_q))^2 / sum_q h_q^2) over the windowed
+ *                    samples (Eq. alps_relative_rmse; 0 when every h_q is 0)
+ *   d_stats[4 j + 1] sigma2_phys = (1/|D|) sum_q w_q h_q^2 over the windowed samples
+ *   d_stats[4 j + 2] sigma2_spec over the selected set, (m, n) != (0, 0)
+ *   d_stats[4 j + 3] sigma2_spec over the whole P x P box, (m, n) != (0, 0)   (Eq. spectral_variance)
+ * The paper evaluates these on deplaned elevations (h minus the cell's weighted mean); the call
+ * uses h as given.  k_max is the row length of d_sel (1..64).  Not built for n_f = 256 and plain
+ * plans (ENUFFT_ERR_UNSUPPORTED); NULL pointers or a bad k_max return ENUFFT_ERR_ARG.
+ */
+enufft_status enufft_reconstruct(enufft_plan plan, const void *d_coeffs, const int32_t *d_kstar,
+                                 const int32_t *d_sel, int k_max, const void *d_x, const void *d_y,
+                                 const void *d_h, const void *d_w, void *d_hrec, double *d_stats);
+
 /* Re-bind the plan to another stream of the same device (e.g. the caller's current stream);
  * work already queued on the old stream is not waited for.  NULL selects the legacy default. */
 enufft_status enufft_set_stream(enufft_plan plan, void *cuda_stream);

@@ -73,9 +73,10 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_last_error.restype = ctypes.c_char_p
     lib.enufft_get_plan_info.argtypes = [vp, P(_Info)]
     lib.enufft_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint]
+    lib.enufft_reconstruct.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
     for f in ("enufft_plan_create", "enufft_plan_destroy", "enufft_type1", "enufft_ems", "enufft_type1_ems",
               "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status", "enufft_set_stream",
-              "enufft_get_plan_info", "enufft_selftest_wait_timeout"):
+              "enufft_get_plan_info", "enufft_selftest_wait_timeout", "enufft_reconstruct"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -168,6 +169,20 @@ class Plan:
         i = _Info()
         self._check(self._lib.enufft_get_plan_info(self._h, ctypes.byref(i)), "get_plan_info")
         return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def reconstruct(self, coeffs, kstar, sel, x, y, h, w, want_hrec: bool = True):
+        """Sec. 3.2 diagnostics (see enufft_reconstruct): (h_rec at the samples or None,
+        stats[n_cells, 4] float64 = eps_rel, sigma2_phys, sigma2_spec over the selection, over the box)."""
+        x, y, h, w = self._samples(x, y, h, w)
+        hrec = torch.empty_like(h) if want_hrec else None
+        stats = torch.empty(self.n_cells, 4, dtype=torch.float64, device=h.device)
+        ks = kstar.to(torch.int32).contiguous()
+        sl = sel.to(torch.int32).contiguous()
+        self._bind()
+        self._check(self._lib.enufft_reconstruct(self._h, _ptr(coeffs.contiguous()), _ptr(ks), _ptr(sl), sl.shape[1],
+                                                 _ptr(x), _ptr(y), _ptr(h), _ptr(w), _ptr(hrec), _ptr(stats)),
+                    "reconstruct")
+        return hrec, stats
 
     def selftest_wait_timeout(self, polls: int = 64):
         """Latch a bounded-wait timeout on the device (see enufft_selftest_wait_timeout)."""

@@ -8,6 +8,11 @@
 //   2. a real n_f x n_f grid g = IFFT2(F) is formed (columns m = 0..P/2, then rows in pairs),
 //   3. v_q = sum_r g_r phi(s_q - r) is interpolated with the spreading kernel (no atomics),
 //   4. dL/dh_q = win_q w_q v_q / |D| and dL/dw_q = win_q h_q v_q / |D| are written.
+//
+// Reconstruction mode (Sec. 3.2 diagnostics): G is the cell's coefficients restricted to the
+// selected mode pairs and their partners, so v_q is the truncated series h_rec (Eq. tri_series) at
+// the samples; per cell the kernel also reduces the relative reconstructed RMSE
+// (Eq. alps_relative_rmse) and the physical and spectral variances of Eq. spectral_variance.
 #pragma once
 
 #include "forward.cuh"
@@ -23,6 +28,12 @@ struct AdjArgs {
     const T* __restrict__ gcoef;   // [n_cells][P][P] complex
     T* __restrict__ grad_h;        // may be null
     T* __restrict__ grad_w;        // may be null
+    int mode;                      // 0: gradient from G; 1: reconstruction diagnostics from coefficients
+    const int32_t* __restrict__ kstar;   // mode 1: selected pairs per cell
+    const int32_t* __restrict__ sel;     // mode 1: [n_cells][k_max] pair indices
+    int k_max;
+    T* __restrict__ hrec;          // mode 1: h_rec at the samples (may be null)
+    double* __restrict__ stats;    // mode 1: [n_cells][4] eps_rel, sigma2_phys, sigma2_spec(set), sigma2_spec(box)
     const int64_t* __restrict__ offsets;
     const CellConst* __restrict__ cells;
     const int* __restrict__ order;
@@ -48,6 +59,32 @@ __device__ __forceinline__ float gather_taps(const float* __restrict__ g, const 
     } else {
         return acc;
     }
+}
+
+// block-wide sums of two doubles (every thread calls; thread 0 receives the totals); scratch holds
+// 2 doubles per warp
+__device__ __forceinline__ void block_sum2(double& u, double& v, double* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        scratch[2 * warp] = u;
+        scratch[2 * warp + 1] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u = 0.0;
+        v = 0.0;
+        for (int i = 0; i < nw; ++i) {
+            u += scratch[2 * i];
+            v += scratch[2 * i + 1];
+        }
+    }
+    __syncthreads();
 }
 
 template <typename T, int NF, int W>
@@ -82,9 +119,36 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
             const float4* s4 = reinterpret_cast<const float4*>(a.gcoef + (size_t)cell * P * P * 2);
             float4* d4 = reinterpret_cast<float4*>(stage);
             const int n4 = P * P * (int)sizeof(cplx<T>) / 16;
-            for (int i = tid; i < n4; i += CF::NT) d4[i] = s4[i];
+            if (a.mode == 0)
+                for (int i = tid; i < n4; i += CF::NT) d4[i] = s4[i];
+            else
+                for (int i = tid; i < n4; i += CF::NT) d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
+        double spec_set = 0.0, spec_all = 0.0;   // mode 1, block totals in thread 0
+        if (a.mode == 1) {
+            // the selected pairs and their partners; sigma2_spec over them and over the box (no DC)
+            const cplx<T>* cf = reinterpret_cast<const cplx<T>*>(a.gcoef) + (size_t)cell * P * P;
+            const int dcp = half * P + half;
+            for (int i = tid; i < P * P; i += CF::NT)
+                if (i != dcp) spec_all += (double)cf[i].re * cf[i].re + (double)cf[i].im * cf[i].im;
+            int K = a.kstar[cell];
+            K = K < 0 ? 0 : (K > a.k_max ? a.k_max : K);
+            for (int k = tid; k < K; k += CF::NT) {
+                const int p = a.sel[(size_t)cell * a.k_max + k];
+                if (p < 0 || p >= P * P) continue;
+                const int n = p / P - half, m = p % P - half;
+                const int nn = half - n, mm = half - m;   // partner (-m, -n) in box coordinates
+                stage[p] = cf[p];
+                if (p != dcp) spec_set += (double)cf[p].re * cf[p].re + (double)cf[p].im * cf[p].im;
+                if (nn >= 0 && nn < P && mm >= 0 && mm < P && nn * P + mm != p) {
+                    const int pp = nn * P + mm;
+                    stage[pp] = cf[pp];
+                    spec_set += (double)cf[pp].re * cf[pp].re + (double)cf[pp].im * cf[pp].im;
+                }
+            }
+            block_sum2(spec_set, spec_all, reinterpret_cast<double*>(sC1));
+        }
         // ---- 1. Hermitian, pre-corrected half spectrum F[n][m], m = 0..P/2, all n rows (zero padded)
         for (int i = tid; i < NF * C1S; i += CF::NT) {
             const int m = i % C1S, nr = i / C1S;            // nr = n mod n_f
@@ -159,7 +223,8 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
             sgrid[r * GS + c] = sgrid[r * GS + cw];
         }
         __syncthreads();
-        // ---- 3+4. interpolate at the samples and scale
+        // ---- 3+4. interpolate at the samples and scale (mode 1: reconstruction and its sums)
+        T s_err = T(0), s_h2 = T(0), s_wh2 = T(0);
         if (scc->valid) {
             const CellConst& cc = *scc;
             const FastFrame ff = fast_frame(cc);
@@ -185,6 +250,16 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                         }
                     }
                 }
+                if (a.mode == 1) {
+                    if (in) {
+                        const T d = ph - v;
+                        s_err += d * d;
+                        s_h2 += ph * ph;
+                        s_wh2 += pw * ph * ph;
+                    }
+                    if (a.hrec) a.hrec[q] = in ? v : T(0);
+                    continue;
+                }
                 T gh = T(0), gw = T(0);
                 if (in) {
                         if constexpr (sizeof(T) == 4) {
@@ -203,6 +278,20 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
             for (int64_t q = q0 + tid; q < q1; q += CF::NT) {
                 if (a.grad_h) a.grad_h[q] = T(0);
                 if (a.grad_w) a.grad_w[q] = T(0);
+                if (a.hrec) a.hrec[q] = T(0);
+            }
+        }
+        if (a.mode == 1) {
+            double e2 = (double)s_err, h2 = (double)s_h2, wh2 = (double)s_wh2, dummy = 0.0;
+            double* scratch = reinterpret_cast<double*>(sC1);   // the column workspace is free here
+            block_sum2(e2, h2, scratch);
+            block_sum2(wh2, dummy, scratch);
+            if (tid == 0) {
+                double* st = a.stats + 4 * (size_t)cell;
+                st[0] = h2 > 0.0 ? sqrt(e2 / h2) : 0.0;
+                st[1] = scc->valid ? wh2 / scc->area : 0.0;
+                st[2] = spec_set;
+                st[3] = spec_all;
             }
         }
     }

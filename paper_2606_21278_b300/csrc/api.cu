@@ -864,9 +864,10 @@ enufft_status enufft_ems_backward(enufft_plan p, const void* d_coeffs, const dou
 
 template <typename T>
 static enufft_status run_adjoint(enufft_plan p, const void* g, const void* x, const void* y, const void* h,
-                                 const void* w, void* gh, void* gw) {
+                                 const void* w, void* gh, void* gw, const AdjArgs<T>* recon = nullptr) {
     AdjArgs<T> a;
     memset(&a, 0, sizeof(a));
+    if (recon) a = *recon;
     a.x = (const T*)x;
     a.y = (const T*)y;
     a.h = (const T*)h;
@@ -892,6 +893,37 @@ static enufft_status run_adjoint(enufft_plan p, const void* g, const void* x, co
     e = launch_adjoint(a, p->NF, p->W, grid, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "type1_backward: launch");
     return ENUFFT_OK;
+}
+
+template <typename T>
+static enufft_status run_reconstruct(enufft_plan p, const void* coeffs, const int32_t* kstar, const int32_t* sel,
+                                     int k_max, const void* x, const void* y, const void* h, const void* w, void* hrec,
+                                     double* stats) {
+    AdjArgs<T> r;
+    memset(&r, 0, sizeof(r));
+    r.mode = 1;
+    r.kstar = kstar;
+    r.sel = sel;
+    r.k_max = k_max;
+    r.hrec = (T*)hrec;
+    r.stats = stats;
+    return run_adjoint<T>(p, coeffs, x, y, h, w, nullptr, nullptr, &r);
+}
+
+extern "C" enufft_status enufft_reconstruct(enufft_plan p, const void* d_coeffs, const int32_t* d_kstar,
+                                            const int32_t* d_sel, int k_max, const void* d_x, const void* d_y,
+                                            const void* d_h, const void* d_w, void* d_hrec, double* d_stats) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "reconstruct: NULL plan");
+    if (k_max < 1 || k_max > kEmsMaxK) return fail(p, ENUFFT_ERR_ARG, "reconstruct: k_max must be in [1, 64]");
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || !d_kstar || !d_sel || !d_stats || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
+        return fail(p, ENUFFT_ERR_ARG, "reconstruct: NULL data pointer");
+    if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "reconstruct: coeffs must be 16-byte aligned");
+    if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for n_f = 256 plans");
+    if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for plain FP32 plans");
+    cudaSetDevice(p->device);
+    return p->dbl ? run_reconstruct<double>(p, d_coeffs, d_kstar, d_sel, k_max, d_x, d_y, d_h, d_w, d_hrec, d_stats)
+                  : run_reconstruct<float>(p, d_coeffs, d_kstar, d_sel, k_max, d_x, d_y, d_h, d_w, d_hrec, d_stats);
 }
 
 extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad_coeffs, const void* d_x,
