@@ -323,6 +323,40 @@ def run_ours(args):
                   "ems_identical": bool(np.array_equal(oks, ks[cells].cpu().numpy()) and
                                         np.array_equal(osel, sel[cells].cpu().numpy()))}
 
+    # Sec. 3.2 diagnostics on the benchmarked spectra and selection (reconstruction at every sample,
+    # relative RMSE, Parseval variances), timed like the step; fused-route plans only
+    recon = None
+    if not args.no_reconstruct and info["cells_large"] == 0:
+        hrec = torch.empty_like(wl.h)
+        stats = torch.empty(wl.n_cells, 4, dtype=torch.float64, device="cuda")
+
+        def rstep():
+            st = lib.enufft_reconstruct(plan._h, ptr(coeffs), ptr(ks), ptr(sel), prm.k_max, ptr(wl.x), ptr(wl.y),
+                                        ptr(wl.h), ptr(wl.w), ptr(hrec), ptr(stats))
+            if st != 0:
+                raise RuntimeError(lib.enufft_last_error(plan._h).decode())
+
+        for _ in range(3):
+            rstep()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rsteps = max(3, min(args.steps, 20))
+        r0.record(stream)
+        for _ in range(rsteps):
+            rstep()
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rms = _max_over_ranks(r0.elapsed_time(r1), ws) / rsteps
+        plan.sync_status()
+        rbytes = 20 * wl.n_points + (8 * P * P + 4 + 4 * prm.k_max + 32) * wl.n_cells
+        rach = rbytes / (rms * 1e-3) / 1e9
+        recon = {"ms": rms, "value": pts_all / (rms * 1e-3), "unit": "points/s", "steps": rsteps,
+                 "kernel": f"type1_adjoint_kernel<float,{info['fine_grid']},{info['kernel_width']}> (reconstruction mode)",
+                 "roofline": {"bound": "hbm", "achieved": rach, "peak": peak, "unit": "GB/s", "frac": rach / peak,
+                              "algorithmic_bytes_per_launch": rbytes},
+                 "median_eps_rel": float(stats[:, 0].median().item())}
+
     # the plain binary32 per-cell path on the same workload (one launch sequence per cell), for the
     # speed-up the metric states; timed the same way, fewer steps
     plain = None
@@ -376,6 +410,7 @@ def run_ours(args):
                 "e2e": {"value": pts_all / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "plain_fp32": plain,
+                "reconstruct": recon,
                 "gpu_launches": info["kernels_per_type1_ems"] * args.steps,
                 "clocks": clk.summary(), "parity": parity}
         print(json.dumps(line), flush=True)
@@ -400,6 +435,7 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
+    ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
