@@ -45,11 +45,12 @@ def lib():
                                           vp, vp, vp, vp, i32]
         _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, vp, vp, vp, vp]
         _lib.oracle_ems_grad_coeffs.argtypes = [i64, i32, vp, vp, i32, i32, vp, vp, vp, vp]
+        _lib.oracle_voronoi_weights_f32.argtypes = [i64, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, i32]
         _lib.oracle_reconstruct_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp,
                                                   vp, i32]
         for f in ("oracle_frame", "oracle_window", "oracle_type1_batch", "oracle_type1_backward_batch",
                   "oracle_ems_batch", "oracle_ems_energies", "oracle_ems_grad_coeffs",
-                  "oracle_threads_used", "oracle_reconstruct_batch"):
+                  "oracle_threads_used", "oracle_reconstruct_batch", "oracle_voronoi_weights_f32"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -134,6 +135,20 @@ def type1_backward(wl, G: np.ndarray, nthreads: int = 0):
                                           int(nthreads))
     assert r == 0
     return gh, gw
+
+
+def voronoi_weights(wl, Ng: int = 64, nthreads: int = 0):
+    """App. A Voronoi weights by raster sampling for binary32 samples: (w[n_points] float32,
+    counts[n_points] int32, -1 for samples outside their window); see oracle_voronoi_weights_f32."""
+    off, nv, vv = _cells(wl)
+    x = np.ascontiguousarray(np.asarray(wl.x.cpu() if hasattr(wl.x, "cpu") else wl.x, dtype=np.float32))
+    y = np.ascontiguousarray(np.asarray(wl.y.cpu() if hasattr(wl.y, "cpu") else wl.y, dtype=np.float32))
+    w = np.zeros(len(x), dtype=np.float32)
+    cnt = np.zeros(len(x), dtype=np.int32)
+    r = lib().oracle_voronoi_weights_f32(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), float(wl.eta),
+                                         int(wl.mask), int(Ng), _p(w), _p(cnt), int(nthreads))
+    assert r == 0, "oracle_voronoi_weights_f32 failed"
+    return w, cnt
 
 
 def selection_mask(kstar, sel, P: int) -> np.ndarray:

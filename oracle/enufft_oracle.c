@@ -16,6 +16,8 @@
  *               "alpha_c", "f_cum", "k_elastic" (+ the footnote bounding all sums by J_max)
  *   gradient    derivative of the EMS-retained power with the selected set held fixed; it is the
  *               adjoint (type-2 sum) of the quadrature above
+ *   weights     App. A Voronoi weights by raster sampling (Eqs. "voronoi_cell", "raster_grid",
+ *               "nn_assignment", "raster_area", "area_partition", "voronoi_weights")
  *   diagnostics Sec. 3.2: the truncated series h_rec (Eq. "tri_series") over a set of modes at the
  *               samples, the relative reconstructed RMSE (Eq. "alps_relative_rmse") and the physical
  *               and spectral variances of Parseval's check (Eq. "spectral_variance")
@@ -275,6 +277,63 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
             grad_h[q] = w[q] * v / f.area;
             grad_w[q] = h[q] * v / f.area;
         }
+    }
+    return err ? -1 : 0;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* App. A: Voronoi quadrature weights by raster sampling                                       */
+/* ----------------------------------------------------------------------------------------- */
+
+/* Exported, for binary32 samples.  Per cell: raster points g_ab at the centres of an Ng x Ng grid
+ * over B (Eq. raster_grid), X = (cx - H) + (L/Ng)(a + 1/2), Y = (cy - H) + (L/Ng)(b + 1/2) in binary64;
+ * kept when in the window (Eq. raster_grid's subset G).  Each kept point goes to the nearest windowed
+ * sample (Eq. nn_assignment); the decision is taken in binary32 -- X, Y rounded to binary32, then
+ * d2 = (X - x_q)^2 + (Y - y_q)^2 with every operation rounded -- and a tie goes to the lowest sample
+ * index.  n_q counts the points of sample q; A_q = n_q |D| / |G| (Eq. raster_area).  A windowed sample
+ * with n_q = 0 takes the floor n_q = 1/2 and all are renormalised to sum to |D| (Eq. area_partition),
+ * so w_q = max(n_q, 1/2) (|D| / sum_q' max(n_q', 1/2)) in binary64, rounded once to binary32 (with
+ * no empty cell this is A_q).  Samples outside the window get w = 0 and count -1. */
+int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
+                               const double *verts, const float *x, const float *y, double eta, int mask,
+                               int Ng, float *w, int32_t *counts, int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : err)
+#endif
+    for (int64_t j = 0; j < n_cells; ++j) {
+        oframe f;
+        const int64_t q0 = offsets[j], q1 = offsets[j + 1];
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) {
+            for (int64_t q = q0; q < q1; ++q) { w[q] = 0.0f; counts[q] = -1; }
+            err |= 1;
+            continue;
+        }
+        for (int64_t q = q0; q < q1; ++q) counts[q] = in_window(&f, (double)x[q], (double)y[q]) ? 0 : -1;
+        const double x0 = f.cx - f.H, y0 = f.cy - f.H, step = f.L / Ng;
+        for (int b = 0; b < Ng; ++b) {
+            for (int a2 = 0; a2 < Ng; ++a2) {
+                const double X = x0 + step * (a2 + 0.5), Y = y0 + step * (b + 0.5);
+                if (!in_window(&f, X, Y)) continue;
+                const float Xf = (float)X, Yf = (float)Y;
+                float best = 0.0f;
+                int64_t arg = -1;
+                for (int64_t q = q0; q < q1; ++q) {
+                    if (counts[q] < 0) continue;
+                    const float dx = Xf - x[q], dy = Yf - y[q];
+                    const float d2 = dx * dx + dy * dy;
+                    if (arg < 0 || d2 < best) { best = d2; arg = q; }
+                }
+                if (arg >= 0) counts[arg] += 1;
+            }
+        }
+        double s = 0.0;   /* sum of max(n_q, 1/2): a multiple of 1/2, exact */
+        for (int64_t q = q0; q < q1; ++q)
+            if (counts[q] >= 0) s += counts[q] > 0 ? (double)counts[q] : 0.5;
+        const double unit = s > 0.0 ? f.area / s : 0.0;
+        for (int64_t q = q0; q < q1; ++q)
+            w[q] = counts[q] < 0 ? 0.0f : (float)((counts[q] > 0 ? (double)counts[q] : 0.5) * unit);
     }
     return err ? -1 : 0;
 }

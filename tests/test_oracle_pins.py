@@ -440,3 +440,57 @@ def test_reconstruction_from_no_modes():
     hrec, st = oracle.reconstruct(wl, c, np.zeros((2, 64, 64), dtype=np.uint8))
     assert np.all(hrec == 0) and np.allclose(st[:, 0], 1.0) and np.all(st[:, 2] == 0)
     assert np.all(st[:, 3] > 0) and np.all(st[:, 1] > 0)
+
+
+# ----------------------------------------------------------------------------------------------
+# Voronoi quadrature weights by raster sampling (App. A, Eqs. raster_grid .. voronoi_weights)
+# ----------------------------------------------------------------------------------------------
+
+def _square_cell(xs, ys, half=0.5):
+    """One square cell [-half, half]^2 (window = the square) with the given binary32 samples."""
+    n = len(xs)
+    wl = synth.regular_grid_square_cell(1, lambda a, b: torch.zeros_like(a), half=half, dtype=torch.float32)
+    return synth.Workload(**{**wl.__dict__, "x": torch.tensor(xs, dtype=torch.float32),
+                             "y": torch.tensor(ys, dtype=torch.float32), "h": torch.zeros(n, dtype=torch.float32),
+                             "w": torch.zeros(n, dtype=torch.float32),
+                             "offsets": torch.tensor([0, n], dtype=torch.int64)})
+
+
+def test_voronoi_weights_of_a_lattice_are_equal():
+    """Samples at the midpoints of an n x n lattice with Ng = 2n raster points per side: every sample is
+    nearest to exactly its own 2 x 2 block of raster points, so every weight is |D| / n^2."""
+    n = 12
+    wl = synth.regular_grid_square_cell(n, lambda a, b: torch.zeros_like(a), half=0.6, offset=0.5, dtype=torch.float32)
+    w, cnt = oracle.voronoi_weights(wl, Ng=2 * n)
+    assert np.all(cnt == 4)
+    assert np.allclose(w, (1.2 ** 2) / n ** 2, rtol=1e-6, atol=0)
+
+
+def test_voronoi_weights_split_at_the_bisector():
+    """Two samples mirrored about x = 0 in the unit square: the bisector splits the raster evenly."""
+    w, cnt = oracle.voronoi_weights(_square_cell([-0.2, 0.2], [0.1, 0.1]), Ng=32)
+    assert cnt.tolist() == [512, 512] and np.allclose(w, [0.5, 0.5], rtol=1e-7)
+
+
+def test_voronoi_duplicate_sample_takes_the_floor():
+    """A coincident second sample loses every tie (lowest index wins), gets the floor 1/2 and the weights
+    still partition the area (Eq. area_partition)."""
+    w, cnt = oracle.voronoi_weights(_square_cell([-0.1, -0.1, 0.3], [0.2, 0.2, -0.25]), Ng=40)
+    assert cnt[1] == 0 and cnt[0] > 0 and cnt[2] > 0 and cnt[0] + cnt[2] == 40 * 40
+    s = cnt[0] + cnt[2] + 0.5
+    assert abs(w[1] - 0.5 / s) < 1e-7 and abs(w.sum() - 1.0) < 1e-6
+
+
+def test_voronoi_weights_partition_the_window():
+    """Triangles: the weights of the windowed samples sum to |D|, every windowed sample has a positive
+    weight, and samples outside the window get none."""
+    wl = synth.make("tri20480_p64", seed=8, n_cells=3, q_scale=0.05)
+    wl.x[int(wl.offsets[1]) + 2] += 50.0           # one sample far outside its window
+    w, cnt = oracle.voronoi_weights(wl, Ng=48)
+    for j in range(3):
+        a, b = int(wl.offsets[j]), int(wl.offsets[j + 1])
+        area = oracle.frame(int(wl.nverts[j]), wl.verts[j], wl.eta, wl.mask)["area"]
+        assert abs(w[a:b].sum() - area) < 1e-5 * area
+        inside = cnt[a:b] >= 0
+        assert np.all(w[a:b][inside] > 0) and np.all(w[a:b][~inside] == 0)
+    assert cnt[int(wl.offsets[1]) + 2] == -1
