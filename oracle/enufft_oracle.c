@@ -293,7 +293,8 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
  * index.  n_q counts the points of sample q; A_q = n_q |D| / |G| (Eq. raster_area).  A windowed sample
  * with n_q = 0 takes the floor n_q = 1/2 and all are renormalised to sum to |D| (Eq. area_partition),
  * so w_q = max(n_q, 1/2) (|D| / sum_q' max(n_q', 1/2)) in binary64, rounded once to binary32 (with
- * no empty cell this is A_q).  Samples outside the window get w = 0 and count -1. */
+ * no empty cell this is A_q).  Samples outside the window, and samples with a non-finite
+ * coordinate, get w = 0 and count -1. */
 int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
                                const double *verts, const float *x, const float *y, double eta, int mask,
                                int Ng, float *w, int32_t *counts, int nthreads) {
@@ -310,7 +311,9 @@ int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const in
             err |= 1;
             continue;
         }
-        for (int64_t q = q0; q < q1; ++q) counts[q] = in_window(&f, (double)x[q], (double)y[q]) ? 0 : -1;
+        /* a sample with a non-finite coordinate is not a point of D: no Voronoi cell, no weight */
+        for (int64_t q = q0; q < q1; ++q)
+            counts[q] = (isfinite(x[q]) && isfinite(y[q]) && in_window(&f, (double)x[q], (double)y[q])) ? 0 : -1;
         const double x0 = f.cx - f.H, y0 = f.cy - f.H, step = f.L / Ng;
         for (int b = 0; b < Ng; ++b) {
             for (int a2 = 0; a2 < Ng; ++a2) {
