@@ -167,6 +167,21 @@ enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs,
                                     void *d_grad_w);
 
 /*
+ * Voronoi quadrature weights by raster sampling (App. A, Eqs. raster_grid .. voronoi_weights) for
+ * the samples of every cell, on the plan's stream, binary32 plans only (binary64 plans return
+ * ENUFFT_ERR_UNSUPPORTED):
+ *   - raster points at the centres of an ng x ng grid over the cell's square B, kept when inside
+ *     the window (the plan's mask);
+ *   - each kept point goes to its nearest windowed sample (squared distance in binary32, every
+ *     operation rounded as written, ties to the lowest sample index); n_q counts its points;
+ *   - d_w[q] = max(n_q, 1/2) |D| / sum_q' max(n_q', 1/2) (a sample no point reached takes the
+ *     floor 1/2; the weights of a cell sum to |D|), 0 for samples outside the window.
+ * d_w [N] binary32 (caller-owned) is also the count scratch while the call runs.  ng in [2, 1024];
+ * the work is ng^2 x (windowed samples) distance evaluations per cell.
+ */
+enufft_status enufft_voronoi_weights(enufft_plan plan, const void *d_x, const void *d_y, int ng, void *d_w);
+
+/*
  * Reconstruction diagnostics of Sec. 3.2 from coefficients and an EMS selection (as written by
  * enufft_type1_ems / enufft_ems on this plan).  The mode set is the selected pairs and their
  * partners: for k < kstar[j], p = sel[j][k] marks (m, n) with p = (n + P/2) P + (m + P/2), and

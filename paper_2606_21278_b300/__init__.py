@@ -74,9 +74,11 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_get_plan_info.argtypes = [vp, P(_Info)]
     lib.enufft_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint]
     lib.enufft_reconstruct.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.enufft_voronoi_weights.argtypes = [vp, vp, vp, i32, vp]
     for f in ("enufft_plan_create", "enufft_plan_destroy", "enufft_type1", "enufft_ems", "enufft_type1_ems",
               "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status", "enufft_set_stream",
-              "enufft_get_plan_info", "enufft_selftest_wait_timeout", "enufft_reconstruct"):
+              "enufft_get_plan_info", "enufft_selftest_wait_timeout", "enufft_reconstruct",
+              "enufft_voronoi_weights"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -169,6 +171,14 @@ class Plan:
         i = _Info()
         self._check(self._lib.enufft_get_plan_info(self._h, ctypes.byref(i)), "get_plan_info")
         return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def voronoi_weights(self, x, y, ng: int = 64) -> torch.Tensor:
+        """Voronoi quadrature weights by raster sampling (see enufft_voronoi_weights)."""
+        x, y = self._samples(x, y)
+        w = torch.empty_like(x)
+        self._bind()
+        self._check(self._lib.enufft_voronoi_weights(self._h, _ptr(x), _ptr(y), int(ng), _ptr(w)), "voronoi_weights")
+        return w
 
     def reconstruct(self, coeffs, kstar, sel, x, y, h, w, want_hrec: bool = True):
         """Sec. 3.2 diagnostics (see enufft_reconstruct): (h_rec at the samples or None,

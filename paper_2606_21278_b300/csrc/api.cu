@@ -910,6 +910,18 @@ static enufft_status run_reconstruct(enufft_plan p, const void* coeffs, const in
     return run_adjoint<T>(p, coeffs, x, y, h, w, nullptr, nullptr, &r);
 }
 
+extern "C" enufft_status enufft_voronoi_weights(enufft_plan p, const void* d_x, const void* d_y, int ng, void* d_w) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "voronoi_weights: NULL plan");
+    if (ng < 2 || ng > 1024) return fail(p, ENUFFT_ERR_ARG, "voronoi_weights: ng must be in [2, 1024]");
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (p->n_points > 0 && (!d_x || !d_y || !d_w)) return fail(p, ENUFFT_ERR_ARG, "voronoi_weights: NULL data pointer");
+    if (p->dbl) return fail(p, ENUFFT_ERR_UNSUPPORTED, "voronoi_weights: binary32 samples only");
+    cudaSetDevice(p->device);
+    cudaError_t e = launch_voronoi((const float*)d_x, (const float*)d_y, p->d_offsets, p->d_cells, (int)p->n_cells, ng,
+                                   (float*)d_w, p->d_ctr + 2, p->num_sms, p->stream);
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "voronoi_weights: launch");
+}
+
 extern "C" enufft_status enufft_reconstruct(enufft_plan p, const void* d_coeffs, const int32_t* d_kstar,
                                             const int32_t* d_sel, int k_max, const void* d_x, const void* d_y,
                                             const void* d_h, const void* d_w, void* d_hrec, double* d_stats) {

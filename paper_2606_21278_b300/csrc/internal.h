@@ -63,6 +63,10 @@ cudaError_t tc_prepare();
 cudaError_t launch_wait_timeout(unsigned polls, unsigned* status, cudaStream_t s);
 cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s);
 
+// Voronoi quadrature weights by raster sampling (voronoi.cu), binary32 samples.
+cudaError_t launch_voronoi(const float* x, const float* y, const int64_t* offsets, const CellConst* cells, int n_cells,
+                           int Ng, float* w, unsigned* status, int num_sms, cudaStream_t s);
+
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).
 void set_thread_error(const std::string& msg);
 

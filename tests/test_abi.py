@@ -86,4 +86,5 @@ def test_null_arguments_are_errors(lib):
     assert lib.enufft_ems(None, None, None, 0, ctypes.byref(e), None, None, None) == 1
     assert lib.enufft_selftest_wait_timeout(None, 8) == 1
     assert lib.enufft_reconstruct(None, None, None, None, 12, None, None, None, None, None, None) == 1
+    assert lib.enufft_voronoi_weights(None, None, None, 64, None) == 1
     assert lib.enufft_plan_destroy(None) == 0
