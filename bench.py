@@ -357,6 +357,36 @@ def run_ours(args):
                               "algorithmic_bytes_per_launch": rbytes},
                  "median_eps_rel": float(stats[:, 0].median().item())}
 
+    # Voronoi quadrature weights by raster sampling (App. A) for the workload's samples, ng = 64:
+    # brute-force nearest windowed sample, ng^2 x Q distance evaluations per cell; binary32 plans of
+    # the fused route only (the brute force is quadratic in the cell size)
+    voronoi = None
+    if not args.no_voronoi and info["cells_large"] == 0 and wl.x.dtype == torch.float32:
+        ng = 64
+        wv = torch.empty_like(wl.w)
+
+        def vstep():
+            st = lib.enufft_voronoi_weights(plan._h, ptr(wl.x), ptr(wl.y), ng, ptr(wv))
+            if st != 0:
+                raise RuntimeError(lib.enufft_last_error(plan._h).decode())
+
+        vstep()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vsteps = 3
+        v0.record(stream)
+        for _ in range(vsteps):
+            vstep()
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms = _max_over_ranks(v0.elapsed_time(v1), ws) / vsteps
+        plan.sync_status()
+        evals = float(ng * ng) * wl.n_points
+        voronoi = {"ms": vms, "value": pts_all / (vms * 1e-3), "unit": "points/s", "steps": vsteps, "ng": ng,
+                   "distance_evals_per_s": _sum_over_ranks(evals, ws) / (vms * 1e-3),
+                   "kernel": "voronoi_kernel (brute-force nearest sample, binary32)"}
+
     # the plain binary32 per-cell path on the same workload (one launch sequence per cell), for the
     # speed-up the metric states; timed the same way, fewer steps
     plain = None
@@ -411,6 +441,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": d2h},
                 "plain_fp32": plain,
                 "reconstruct": recon,
+                "voronoi": voronoi,
                 "gpu_launches": info["kernels_per_type1_ems"] * args.steps,
                 "clocks": clk.summary(), "parity": parity}
         print(json.dumps(line), flush=True)
@@ -436,6 +467,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
     ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
+    ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
