@@ -449,6 +449,31 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_error_vs_width(args):
+    """Accuracy of the transform against the oracle as a function of the kernel width w on the single
+    equilateral triangle (2000 samples, P = 32, sigma = 2): binary32 (mixed) plans for w = 4..10 and
+    binary64 plans for w = 8..13, with tol = 0 so that w is used as given.  One JSON line."""
+    import oracle
+    import paper_2606_21278_b300 as enufft
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl64 = synth.make("tri1_q2000_p32_fp64", seed=0)
+    ref = oracle.type1(wl64)
+    rows = []
+    for prec, widths in (("mixed", range(4, 11)), ("fp64", range(8, 14))):
+        wl = wl64 if prec == "fp64" else synth.Workload(**{**wl64.__dict__, **{k: getattr(wl64, k).float()
+                                                                                for k in ("x", "y", "h", "w")}})
+        g = wl.to("cuda")
+        for wd in widths:
+            plan = enufft.Plan.for_workload(g, kernel_width=wd, tol=0.0, precision=prec)
+            c = plan.type1(g.x, g.y, g.h, g.w)
+            plan.sync_status()
+            cn = c.cpu().numpy().astype(np.complex128)
+            rows.append({"precision": prec, "w": wd, "fine_grid": plan.info()["fine_grid"],
+                         "rel_l2": float(np.linalg.norm(cn - ref) / np.linalg.norm(ref))})
+    print(json.dumps({"error_vs_width": rows, "workload": "tri1_q2000_p32_fp64", "modes": 32, "sigma": 2.0}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,8 +493,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
     ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
+    ap.add_argument("--error-vs-width", action="store_true",
+                    help="print the rel-l2 error against the oracle for kernel widths 4..13 (single triangle) and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.error_vs_width:
+        run_error_vs_width(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
