@@ -21,7 +21,8 @@ def _close(got, ref):
 
 @pytest.mark.parametrize("name,n,qs,mask,ng", [("tri20480_p64", 6, 0.1, 0, 64), ("hex4096_p48", 4, 0.1, 0, 48),
                                                ("tri20480_p64", 3, 0.1, 1, 40), ("hex4096_p48", 3, 0.1, 2, 64),
-                                               ("tri20480_p64", 2, 0.6, 0, 96)])
+                                               ("tri20480_p64", 2, 0.6, 0, 96),
+                                               ("tri20480_p64", 2, 7.0, 0, 32)])   # > 16384 windowed samples
 def test_voronoi_weights_match_oracle(name, n, qs, mask, ng):
     wl = synth.make(name, seed=12, n_cells=n, q_scale=qs)
     wl.mask = mask
