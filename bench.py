@@ -181,8 +181,10 @@ def run_reference(args):
     wl = _workload(args, seed=0, device="cpu")
     rng = np.random.default_rng(0)
     order = rng.permutation(wl.n_cells)
-    # calibrate on a few cells (warm-up)
-    n = max(2, min(8, wl.n_cells))
+    # calibrate on as many cells as keep every host thread busy (warm-up); the steps below use at
+    # least as many, so the oracle runs at its parallel rate rather than on one or two large cells
+    busy = 4 * (os.cpu_count() or 1)
+    n = max(1, min(busy, wl.n_cells))
     per_point = None
     pos = 0
     for _ in range(max(1, args.warmup)):
@@ -192,7 +194,7 @@ def run_reference(args):
         oracle.ems(oracle.type1(sub))
         per_point = (time.perf_counter() - t0) / max(1, sub.n_points)
     mean_q = wl.n_points / max(1, wl.n_cells)
-    cells_per_step = int(max(1, min(wl.n_cells, args.ref_seconds / max(1, args.steps) / (per_point * mean_q))))
+    cells_per_step = int(max(min(busy, wl.n_cells), min(wl.n_cells, args.ref_seconds / max(1, args.steps) / (per_point * mean_q))))
     pts, secs = 0, 0.0
     for _ in range(args.steps):
         sub = wl.cell_slice(sorted(order[pos:pos + cells_per_step].tolist()))
