@@ -41,9 +41,9 @@ def lib():
         _lib.oracle_type1_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, i32]
         _lib.oracle_type1_backward_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp,
                                                      vp, vp, i32]
-        _lib.oracle_ems_batch.argtypes = [i64, i32, vp, vp, i32, i32, i32, d, d, d, d, d, i32, i32, i32,
+        _lib.oracle_ems_batch.argtypes = [i64, i32, vp, vp, i32, i32, i32, d, d, d, d, d, i32, i32, i32, d,
                                           vp, vp, vp, vp, i32]
-        _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, vp, vp, vp, vp]
+        _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, d, vp, vp, vp, vp]
         _lib.oracle_ems_grad_coeffs.argtypes = [i64, i32, vp, vp, i32, i32, vp, vp, vp, vp]
         _lib.oracle_voronoi_weights_f32.argtypes = [i64, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, i32]
         _lib.oracle_reconstruct_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp,
@@ -83,6 +83,8 @@ class EMSParams:
     w2: float = 0.5
     sum_all: int = 0      # 0 HEAD reading (sums over J_max = min(J*, K_max)), 1 ALL reading (J*)
     include_dc: int = 0
+    sens_eps: float = 2e-5   # relative energy error for the alpha_C sensitivity (twice the 1e-5
+                             # coefficient gate: an energy is a sum of squared moduli)
 
 
 def frame(nverts: int, verts, eta: float = 1.5, mask: int = 0) -> dict:
@@ -187,7 +189,9 @@ def reconstruct(wl, coeffs: np.ndarray, mask: np.ndarray, nthreads: int = 0):
 def ems(coeffs: np.ndarray, params: EMSParams = EMSParams(), mode_weights=None, energy_fp32: bool = False,
         nthreads: int = 0):
     """EMS per spectrum.  Returns (kstar[n], sel[n, K_max] pair indices (-1 padded),
-    retained_power[n], diag[n, 10])."""
+    retained_power[n], diag[n, 12]).  diag columns: N_eff, S_delta, C, alpha_C, total energy,
+    theta(K*), margin_rank, margin_theta, J*, pairs with positive energy, gap at the K_max boundary,
+    alpha_C sensitivity to a relative energy error params.sens_eps (NaN where undefined)."""
     coeffs = np.asarray(coeffs)
     n, P, _ = coeffs.shape
     c = np.ascontiguousarray(np.stack([coeffs.real, coeffs.imag], -1), dtype=np.float64)
@@ -199,27 +203,28 @@ def ems(coeffs: np.ndarray, params: EMSParams = EMSParams(), mode_weights=None, 
     ks = np.zeros(n, dtype=np.int32)
     sel = np.zeros((n, params.k_max), dtype=np.int32)
     ret = np.zeros(n)
-    diag = np.zeros((n, 10))
+    diag = np.zeros((n, 12))
     r = lib().oracle_ems_batch(n, P, _p(c), _p(W) if W is not None else None, per_cell, params.k_min,
                                params.k_max, params.alpha_min, params.alpha_max, params.delta, params.w1,
-                               params.w2, params.sum_all, params.include_dc, int(energy_fp32), _p(ks),
-                               _p(sel), _p(ret), _p(diag), int(nthreads))
+                               params.w2, params.sum_all, params.include_dc, int(energy_fp32),
+                               params.sens_eps, _p(ks), _p(sel), _p(ret), _p(diag), int(nthreads))
     assert r == 0
     return ks, sel, ret, diag
 
 
 def ems_energies(E, params: EMSParams = EMSParams()):
-    """EMS on an explicit energy list.  Returns (K*, selected positions, retained, diag[6])."""
+    """EMS on an explicit energy list.  Returns (K*, selected positions, retained, diag[12]) with the
+    diag columns of ``ems``."""
     E = _f64(E)
     ks = np.zeros(1, dtype=np.int32)
     sel = np.zeros(params.k_max, dtype=np.int32)
     ret = np.zeros(1)
-    diag = np.zeros(10)
+    diag = np.zeros(12)
     r = lib().oracle_ems_energies(len(E), _p(E), params.k_min, params.k_max, params.alpha_min,
                                   params.alpha_max, params.delta, params.w1, params.w2, params.sum_all,
-                                  _p(ks), _p(sel), _p(ret), _p(diag))
+                                  params.sens_eps, _p(ks), _p(sel), _p(ret), _p(diag))
     assert r == 0
-    return int(ks[0]), sel[: int(ks[0])].copy(), float(ret[0]), diag[:6].copy()
+    return int(ks[0]), sel[: int(ks[0])].copy(), float(ret[0]), diag
 
 
 def ems_grad_coeffs(coeffs, kstar, sel, grad_power, k_max: int, mode_weights=None) -> np.ndarray:

@@ -442,20 +442,17 @@ typedef struct {
     int sum_all;      /* 0: HEAD reading (J_max), 1: ALL reading (J*) */
     int include_dc;
     int energy_fp32;
+    double sens_eps;  /* relative energy perturbation of the alpha_C sensitivity (diag[11]) */
 } oems_params;
 
-/* Selection core on an unsorted list of J pair energies (Eqs. sorted_energy .. k_elastic).
- * diag (optional, 10 doubles):
- *   N_eff, S_delta, C, alpha_C, total, theta(K*), margin_rank, margin_theta, J*, n_positive */
-static void ems_select(epair *e, int J, const oems_params *pp, int32_t *kstar, int32_t *sel,
-                       double *retained, double *diag) {
-    qsort(e, J, sizeof(epair), cmp_desc);                       /* Eq. sorted_energy */
+/* N_eff, S_delta, C and alpha_C (Eqs. n_eff, s_delta, c_score, alpha_c) of n energies sorted in
+ * descending order; M1 (the sum that is the denominator of Eq. f_cum) through *m1. */
+static double alpha_of(const epair *e, int J, const oems_params *pp, double *neff_o, double *S_o,
+                       double *C_o, double *m1) {
     int Jmax = J < pp->k_max ? J : pp->k_max;                    /* footnote: J_max = min(J*, K_max) */
     int nsum = pp->sum_all ? J : Jmax;
     double M1 = 0.0, M2 = 0.0;
     for (int j = 0; j < nsum; ++j) { M1 += e[j].E; M2 += e[j].E * e[j].E; }
-    int npos = 0;
-    for (int j = 0; j < J; ++j) npos += e[j].E > 0.0;
     double neff = M2 > 0.0 ? M1 * M1 / M2 : 0.0;                 /* Eq. n_eff */
     double S = 0.0;                                              /* Eq. s_delta */
     if (Jmax >= 2) {
@@ -465,7 +462,50 @@ static void ems_select(epair *e, int J, const oems_params *pp, int32_t *kstar, i
     }
     double nclip = neff < pp->k_max ? neff : (double)pp->k_max;
     double C = pp->w1 * nclip / pp->k_max + pp->w2 * S;          /* Eq. c_score */
-    double alpha = pp->alpha_min + (pp->alpha_max - pp->alpha_min) * C;   /* Eq. alpha_c */
+    if (neff_o) *neff_o = neff;
+    if (S_o) *S_o = S;
+    if (C_o) *C_o = C;
+    if (m1) *m1 = M1;
+    return pp->alpha_min + (pp->alpha_max - pp->alpha_min) * C;  /* Eq. alpha_c */
+}
+
+/* How far alpha_C moves when every energy carries a relative error of eps: the energies in
+ * sorted order are scaled by (1 + s (-1)^j eps) for s = +1 and s = -1 (alternating signs move
+ * every successive ratio of Eq. s_delta by the most, a factor (1 +- eps) / (1 -+ eps); a common
+ * factor would leave alpha_C unchanged), re-sorted, and alpha_C recomputed; the larger of the two
+ * absolute changes. */
+static double alpha_sensitivity(const epair *e, int J, const oems_params *pp, double alpha) {
+    if (J < 1 || !(pp->sens_eps > 0.0)) return 0.0;
+    epair *t = (epair *)malloc(sizeof(epair) * J);
+    if (!t) return NAN;
+    double worst = 0.0;
+    for (int s = -1; s <= 1; s += 2) {
+        for (int j = 0; j < J; ++j) {
+            t[j] = e[j];
+            t[j].E = e[j].E * (1.0 + (double)s * ((j & 1) ? -1.0 : 1.0) * pp->sens_eps);
+        }
+        qsort(t, J, sizeof(epair), cmp_desc);
+        double d = fabs(alpha_of(t, J, pp, NULL, NULL, NULL, NULL) - alpha);
+        if (d > worst) worst = d;
+    }
+    free(t);
+    return worst;
+}
+
+/* Selection core on an unsorted list of J pair energies (Eqs. sorted_energy .. k_elastic).
+ * diag (optional, 12 doubles):
+ *   N_eff, S_delta, C, alpha_C, total, theta(K*), margin_rank, margin_theta, J*, n_positive,
+ *   gap at K_max, alpha_C sensitivity.  margin_rank = (E_(K*) - E_(K*+1)) / E_(K*) and
+ *   margin_theta = min(theta(K*) - alpha_C, alpha_C - theta(K*-1)) say how close the selection is
+ *   to a tie in the ranking or at the threshold of Eq. k_elastic. */
+static void ems_select(epair *e, int J, const oems_params *pp, int32_t *kstar, int32_t *sel,
+                       double *retained, double *diag) {
+    qsort(e, J, sizeof(epair), cmp_desc);                       /* Eq. sorted_energy */
+    int Jmax = J < pp->k_max ? J : pp->k_max;                    /* footnote: J_max = min(J*, K_max) */
+    int npos = 0;
+    for (int j = 0; j < J; ++j) npos += e[j].E > 0.0;
+    double neff, S, C, M1;
+    double alpha = alpha_of(e, J, pp, &neff, &S, &C, &M1);
     double total = M1;                                           /* denominator of Eq. f_cum */
     int K = 0;
     double cum = 0.0, theta_k = 0.0;
@@ -495,8 +535,12 @@ static void ems_select(epair *e, int J, const oems_params *pp, int32_t *kstar, i
             double a = theta_k - alpha, b = alpha - prev;
             mt = a < b ? a : b;
         }
+        double gk = NAN;   /* gap at the K_max boundary: which pairs form the head */
+        if (J > pp->k_max && e[pp->k_max - 1].E > 0.0)
+            gk = (e[pp->k_max - 1].E - e[pp->k_max].E) / e[pp->k_max - 1].E;
         diag[0] = neff; diag[1] = S; diag[2] = C; diag[3] = alpha; diag[4] = total;
         diag[5] = theta_k; diag[6] = mr; diag[7] = mt; diag[8] = J; diag[9] = npos;
+        diag[10] = gk; diag[11] = alpha_sensitivity(e, J, pp, alpha);
     }
 }
 
@@ -526,9 +570,10 @@ static int ems_cell(int P, const double *c, const double *W, const oems_params *
  * (w_per_cell = 0), or one table per cell (w_per_cell = 1). */
 int oracle_ems_batch(int64_t n_cells, int P, const double *coeffs, const double *W, int w_per_cell,
                      int k_min, int k_max, double alpha_min, double alpha_max, double delta, double w1,
-                     double w2, int sum_all, int include_dc, int energy_fp32, int32_t *kstar,
-                     int32_t *sel, double *retained, double *diag, int nthreads) {
-    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, include_dc, energy_fp32};
+                     double w2, int sum_all, int include_dc, int energy_fp32, double sens_eps,
+                     int32_t *kstar, int32_t *sel, double *retained, double *diag, int nthreads) {
+    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, include_dc, energy_fp32,
+                      sens_eps};
     if (k_max < 1 || k_min < 0) return -1;
     int err = 0;
 #ifdef _OPENMP
@@ -538,7 +583,7 @@ int oracle_ems_batch(int64_t n_cells, int P, const double *coeffs, const double 
     for (int64_t j = 0; j < n_cells; ++j) {
         const double *Wj = W ? W + (w_per_cell ? (size_t)P * P * j : 0) : NULL;
         if (ems_cell(P, coeffs + 2 * (size_t)P * P * j, Wj, &pp, kstar + j, sel + (size_t)k_max * j,
-                     retained + j, diag ? diag + 10 * j : NULL))
+                     retained + j, diag ? diag + 12 * j : NULL))
             err |= 1;
     }
     return err ? -1 : 0;
@@ -547,9 +592,9 @@ int oracle_ems_batch(int64_t n_cells, int P, const double *coeffs, const double 
 /* Exported: EMS on an explicit list of J energies (any order), used to check the selection
  * rules on the paper's spectral families; sel receives positions in the input list. */
 int oracle_ems_energies(int J, const double *E, int k_min, int k_max, double alpha_min, double alpha_max,
-                        double delta, double w1, double w2, int sum_all, int32_t *kstar, int32_t *sel,
-                        double *retained, double *diag) {
-    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, 0, 0};
+                        double delta, double w1, double w2, int sum_all, double sens_eps, int32_t *kstar,
+                        int32_t *sel, double *retained, double *diag) {
+    oems_params pp = {k_min, k_max, alpha_min, alpha_max, delta, w1, w2, sum_all, 0, 0, sens_eps};
     if (k_max < 1 || k_min < 0) return -1;
     epair *e = (epair *)malloc(sizeof(epair) * (J > 0 ? J : 1));
     if (!e) return -2;

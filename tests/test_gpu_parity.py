@@ -176,18 +176,22 @@ def test_ems_mode_weights():
 
 def test_ems_end_to_end_against_fp64_oracle():
     """Mode sets from the mixed GPU path equal the FP64 oracle's mode sets, except where the oracle's own
-    margins show a near-tie below the GPU coefficient error."""
+    margins show a near-tie below the GPU coefficient error: a ranking gap (at K* or at the K_max
+    boundary) or a threshold margin within 100x that error, or an alpha_C that moves by more than the
+    threshold margin under an energy error of twice it.  Each mismatch is reported with its margins."""
     wl = synth.make("tri20480_p64", seed=12, n_cells=48, q_scale=0.2)
     g = _gpu(wl)
     plan = enufft.Plan.for_workload(g)
     c, ks, sel, ret = plan.type1_ems(g.x, g.y, g.h, g.w)
     ref = oracle.type1(wl)
-    oks, osel, oret, diag = oracle.ems(ref, OEMS())
     err = _rel_l2(c.cpu().numpy(), ref).max()
+    oks, osel, oret, diag = oracle.ems(ref, OEMS(sens_eps=2 * err))
     bad = np.nonzero((ks.cpu().numpy() != oks) | (sel.cpu().numpy() != osel).any(1))[0]
     for j in bad:
-        margin = np.nanmin(np.abs(diag[j, 6:8]))
-        assert margin < 100 * err, (j, margin, err)
+        m_rank, m_theta, gap_kmax, sens = diag[j, 6], diag[j, 7], diag[j, 10], diag[j, 11]
+        near_tie = np.nanmin(np.abs([m_rank, m_theta, gap_kmax])) < 100 * err or sens >= abs(m_theta)
+        assert near_tie, dict(cell=int(j), margin_rank=m_rank, margin_theta=m_theta, gap_kmax=gap_kmax,
+                              alpha_sensitivity=sens, coeff_err=err)
     assert len(bad) <= 2
     good = np.setdiff1d(np.arange(len(oks)), bad)
     assert np.allclose(ret.cpu().numpy()[good], oret[good], rtol=1e-4)

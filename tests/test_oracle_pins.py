@@ -302,6 +302,41 @@ def test_ems_degenerate_cases():
     assert k == 1 and d[1] == 0.0                                  # J_max < 2: S_delta = 0
 
 
+def test_ems_margins_closed_forms():
+    """Per-cell margins of the selection (near-tie diagnostics), on spectra worked by hand.
+
+    E = (4, 3, 2, 1), K_max = 4, HEAD sums: total 10, N_eff = 100/30, S_delta = (e^(-50/3) + e^(-25) +
+    e^(-50)) / 3 ~ 1.9e-8, C = 0.5 (10/3)/4 + 0.5 S_delta, alpha_C = 0.7 C = 0.291667 (+1.3e-8);
+    theta(1) = 0.4 >= alpha_C, so K* = 1: margin_theta = min(0.4 - alpha_C, alpha_C - 0) = 0.108333,
+    margin_rank = (4 - 3)/4; no gap at K_max (J* = K_max).  With K_max = 3 and K_min = 3 the
+    budget clamps K* to 3: margin_rank = (2 - 1)/2 and the K_max gap is (2 - 1)/2."""
+    k, _, _, d = oracle.ems_energies(np.array([1.0, 4.0, 2.0, 3.0]), EMSParams(k_max=4))
+    assert k == 1
+    assert abs(d[3] - 0.7 * 0.5 * (10 / 3) / 4) < 1e-7
+    assert abs(d[6] - 0.25) < 1e-15
+    assert abs(d[7] - (0.4 - 0.7 * 0.5 * (10 / 3) / 4)) < 1e-7
+    assert math.isnan(d[10])
+    k, _, _, d = oracle.ems_energies(np.array([4.0, 3.0, 2.0, 1.0]), EMSParams(k_min=3, k_max=3))
+    assert k == 3 and abs(d[6] - 0.5) < 1e-15 and abs(d[10] - 0.5) < 1e-15
+
+
+def test_ems_alpha_sensitivity_two_pairs():
+    """Two equal pairs (J* = K_max = 2): N_eff = 2, S_delta = 1, C = 1, alpha_C = 0.7.  A relative
+    error eps on alternate energies gives (1 + eps, 1 - eps): N_eff = 2 / (1 + eps^2) and
+    S_delta = exp(-(2 eps / (1 - eps)) / delta), so alpha_C moves by
+    0.7 - 0.7 (0.5 / (1 + eps^2) + 0.5 exp(-2 eps / ((1 - eps) delta))).  A common factor on every
+    energy changes nothing, and eps = 0 gives 0."""
+    for eps in (1e-3, 2e-5):
+        prm = EMSParams(k_max=2, sens_eps=eps)
+        _, _, _, d = oracle.ems_energies(np.array([1.0, 1.0]), prm)
+        want = 0.7 - 0.7 * (0.5 / (1 + eps * eps) + 0.5 * math.exp(-2 * eps / ((1 - eps) * 0.02)))
+        assert abs(d[3] - 0.7) < 1e-15 and abs(d[11] - want) < 1e-12, (eps, d[11], want)
+        _, _, _, d2 = oracle.ems_energies(np.array([3.5, 3.5]), prm)
+        assert abs(d2[11] - d[11]) < 1e-14
+    _, _, _, d = oracle.ems_energies(np.array([1.0, 1.0]), EMSParams(k_max=2, sens_eps=0.0))
+    assert d[11] == 0.0
+
+
 def test_ems_on_spectrum_pairs_and_indices():
     """A spectrum with two plane waves: the selected pairs are those two, encoded by the half-plane
     member (n > 0, or n = 0 and m > 0), p = (n + P/2) P + (m + P/2); DC is excluded."""
