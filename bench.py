@@ -222,7 +222,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = _workload(args, seed=rank, device="cuda")
-    plan = enufft.Plan.for_workload(wl)
+    plan = enufft.Plan.for_workload(wl, kernel=args.kernel)
     info = plan.info()
     prm = enufft.EMSParams()
     coeffs = plan.new_coeffs()
@@ -393,7 +393,7 @@ def run_ours(args):
     # speed-up the metric states; timed the same way, fewer steps
     plain = None
     if not args.no_plain:
-        pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0)
+        pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0, kernel=args.kernel)
         pco = pplan.new_coeffs()
         lib.enufft_set_stream(pplan._h, ctypes.c_void_p(stream.cuda_stream))
 
@@ -435,7 +435,7 @@ def run_ours(args):
                            **({"q_scale": args.q_scale} if args.q_scale != 1.0 else {}),
                            **({"max_q": args.max_q} if args.max_q is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
-                           "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
+                           "kernel": args.kernel, "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
                            "l2": f"inputs larger than L2 ({16 * wl.n_points / 1e9:.2f} GB of samples per step)",
                            "parallelism": f"cells sharded, {ws} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu_base,
@@ -454,24 +454,26 @@ def run_ours(args):
 def run_error_vs_width(args):
     """Accuracy of the transform against the oracle as a function of the kernel width w on the single
     equilateral triangle (2000 samples, P = 32, sigma = 2): binary32 (mixed) plans for w = 4..10 and
-    binary64 plans for w = 8..13, with tol = 0 so that w is used as given.  One JSON line."""
+    binary64 plans for w = 8..13, with tol = 0 so that w is used as given, for the ES and the KB
+    kernel.  One JSON line."""
     import oracle
     import paper_2606_21278_b300 as enufft
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     wl64 = synth.make("tri1_q2000_p32_fp64", seed=0)
     ref = oracle.type1(wl64)
     rows = []
-    for prec, widths in (("mixed", range(4, 11)), ("fp64", range(8, 14))):
-        wl = wl64 if prec == "fp64" else synth.Workload(**{**wl64.__dict__, **{k: getattr(wl64, k).float()
-                                                                                for k in ("x", "y", "h", "w")}})
-        g = wl.to("cuda")
-        for wd in widths:
-            plan = enufft.Plan.for_workload(g, kernel_width=wd, tol=0.0, precision=prec)
-            c = plan.type1(g.x, g.y, g.h, g.w)
-            plan.sync_status()
-            cn = c.cpu().numpy().astype(np.complex128)
-            rows.append({"precision": prec, "w": wd, "fine_grid": plan.info()["fine_grid"],
-                         "rel_l2": float(np.linalg.norm(cn - ref) / np.linalg.norm(ref))})
+    for kernel in ("es", "kb"):
+        for prec, widths in (("mixed", range(4, 11)), ("fp64", range(8, 14))):
+            wl = wl64 if prec == "fp64" else synth.Workload(**{**wl64.__dict__, **{
+                k: getattr(wl64, k).float() for k in ("x", "y", "h", "w")}})
+            g = wl.to("cuda")
+            for wd in widths:
+                plan = enufft.Plan.for_workload(g, kernel_width=wd, tol=0.0, precision=prec, kernel=kernel)
+                c = plan.type1(g.x, g.y, g.h, g.w)
+                plan.sync_status()
+                cn = c.cpu().numpy().astype(np.complex128)
+                rows.append({"kernel": kernel, "precision": prec, "w": wd, "fine_grid": plan.info()["fine_grid"],
+                             "rel_l2": float(np.linalg.norm(cn - ref) / np.linalg.norm(ref))})
     print(json.dumps({"error_vs_width": rows, "workload": "tri1_q2000_p32_fp64", "modes": 32, "sigma": 2.0}),
           flush=True)
 
@@ -495,6 +497,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
     ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
+    ap.add_argument("--kernel", default="es", choices=["es", "kb"],
+                    help="spreading kernel: exponential of semicircle (default) or Kaiser-Bessel")
     ap.add_argument("--error-vs-width", action="store_true",
                     help="print the rel-l2 error against the oracle for kernel widths 4..13 (single triangle) and exit")
     args = ap.parse_args()

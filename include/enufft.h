@@ -7,7 +7,8 @@
  *     h_mn = 1/|D| sum_q win_q w_q h_q exp(-i (k_m x'_q + k_n y'_q)),   k_m = 2 pi m / L,
  *
  * (App. B, Eq. discrete_quadrature, with the local window of App. A), by a type-1 NUFFT
- * (Sec. 2.1.2: spread, FFT, deconvolve) with an exponential-of-semicircle kernel, and then the
+ * (Sec. 2.1.2: spread, FFT, deconvolve) with an exponential-of-semicircle kernel (or the paper's
+ * Kaiser-Bessel kernel), and then the
  * Elastic Mode Selection of Sec. 2.2 on each spectrum.  It also provides the adjoint (type-2)
  * needed for gradients of the EMS-retained power with respect to the samples and weights.
  *
@@ -59,6 +60,18 @@ typedef enum {
 
 typedef enum { ENUFFT_MASK_CELL = 0, ENUFFT_MASK_SQUARE = 1, ENUFFT_MASK_CIRCLE = 2 } enufft_mask;
 
+/* Spreading kernel (Sec. 2.1.2).  Either choice reaches the same quadrature sum within the
+ * plan's tolerance; the kernel only changes how the spread/FFT/deconvolve route gets there (the
+ * tensor-core direct sum uses no kernel).
+ *   ES: exponential of semicircle phi(z) = exp(beta (sqrt(1 - z^2) - 1)), z = 2 tau / w,
+ *       beta = 2.30 w at sigma = 2 (scaled by (1 - 1/(2 sigma)) / 0.75 otherwise); Phi by
+ *       Gauss-Legendre quadrature at plan time.
+ *   KB: Kaiser-Bessel, Eq. kb_compact with half-width a = w/2 grid points and the shape of
+ *       Eq. kaisal_bessel_coeffs (beta = 2.34, gamma = pi sqrt((2 a beta / pi)^2 - 0.8)),
+ *       normalised to phi(0) = 1 (a constant factor that the deconvolution divides out); Phi
+ *       from the closed form of Eq. kb_fourier. */
+typedef enum { ENUFFT_KERNEL_ES = 0, ENUFFT_KERNEL_KB = 1 } enufft_kernel;
+
 typedef struct {
     int modes;            /* P, retained modes per dimension: even, 2..128                       */
     double oversamp;      /* sigma >= 2: fine grid n_f = smallest power of two >= sigma * P      */
@@ -72,6 +85,7 @@ typedef struct {
                              sum (Eq. discrete_quadrature as a dense contraction); 0 = off.
                              Mixed-precision plans with modes <= 64 only: other plans with a
                              positive value return ENUFFT_ERR_UNSUPPORTED                       */
+    enufft_kernel kernel; /* spreading kernel (default ES)                                       */
 } enufft_opts;
 
 typedef struct {
@@ -84,7 +98,8 @@ typedef struct {
     int include_dc;                   /* 0: the (0,0) mode is not a candidate                     */
 } enufft_ems_params;
 
-/* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path. */
+/* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path,
+ * ES kernel. */
 void enufft_default_opts(enufft_opts *opts);
 /* Defaults of the paper's EMS illustration (Sec. 2.2): K_min 1, K_max 12, alpha 0..0.7,
  * delta 0.02, w1 = w2 = 0.5, HEAD sums, DC excluded. */
@@ -249,10 +264,11 @@ const char *enufft_last_error(enufft_plan plan);
  * NULL plan or output. */
 typedef struct {
     int modes, fine_grid, kernel_width;
-    double beta, oversamp_effective;
+    double beta, oversamp_effective;   /* beta: the kernel's shape (ES beta, or KB gamma)       */
     int64_t n_cells, n_points, cells_fused, cells_tensor, cells_large;
     int precision;
     int64_t cells_plain, kernels_per_type1_ems;
+    int kernel;                        /* enufft_kernel of the plan                             */
 } enufft_plan_info;
 enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.environ.get("ENUFFT_LIB", os.path.join(os.path.dirname(os.path.abs
 _lib = None
 
 _PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
+_KERNEL = {"es": 0, "kb": 1}
 _MASK = {"cell": 0, "square": 1, "circle": 2}
 
 
@@ -29,7 +30,7 @@ class EnufftError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("oversamp", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("tol", ctypes.c_double), ("prec", ctypes.c_int), ("mask", ctypes.c_int),
-                ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int)]
+                ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class _Ems(ctypes.Structure):
@@ -43,7 +44,8 @@ class _Info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("oversamp_effective", ctypes.c_double),
                 ("n_cells", ctypes.c_int64), ("n_points", ctypes.c_int64), ("cells_fused", ctypes.c_int64),
                 ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int),
-                ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64)]
+                ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64),
+                ("kernel", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -115,7 +117,7 @@ class Plan:
 
     def __init__(self, offsets: torch.Tensor, nverts: torch.Tensor, verts: torch.Tensor, modes: int = 64,
                  oversamp: float = 2.0, kernel_width: int = 7, tol: float = 0.0, precision: str = "mixed",
-                 mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0):
+                 mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0, kernel: str = "es"):
         self._lib = load_library()
         if not torch.cuda.is_available():
             raise EnufftError("no CUDA device")
@@ -128,8 +130,10 @@ class Plan:
         self.precision = precision
         self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
         self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        if kernel not in _KERNEL:
+            raise EnufftError(f"kernel must be one of {sorted(_KERNEL)}")
         o = _Opts(modes, oversamp, kernel_width, tol, _PREC[precision],
-                  _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points)
+                  _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points, _KERNEL[kernel])
         h = ctypes.c_void_p()
         st = self._lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), self.n_cells, _ptr(self.offsets),
                                           _ptr(self.nverts), _ptr(self.verts), _stream())

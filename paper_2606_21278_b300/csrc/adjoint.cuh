@@ -240,7 +240,7 @@ type1_adjoint_kernel(const __grid_constant__ AdjArgs<T> a) {
                     if (in) v = gather_taps<W, GS>(sgrid + (r0y + HO) * GS + (r0x + HO), kx, ky, 0.0f, 0.0f);
                 } else {
                     double kx[W], ky[W];
-                    in = prep_f64<NF, W>(cc, a.beta, px, py, r0x, r0y, kx, ky, a.status);
+                    in = prep_f64<NF, W>(cc, a.poly, a.beta, px, py, r0x, r0y, kx, ky, a.status);
                     if (in) {
                         const double* gp = reinterpret_cast<const double*>(sgrid) + (r0y + HO) * GS + (r0x + HO);
                         for (int j = 0; j < W; ++j) {

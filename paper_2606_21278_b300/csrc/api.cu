@@ -132,11 +132,19 @@ static enufft_status cuda_fail(enufft_plan p, cudaError_t e, const char* where) 
                 std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// exponential of semicircle kernel on z in [-1, 1]
-static double es_kernel(double z, double beta) {
-    if (std::fabs(z) > 1.0) return 0.0;
-    return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
-}
+// the spreading kernel on z in [-1, 1] (z = 2 tau / W, tau in grid points), host side in binary64:
+// ES exp(beta (sqrt(1 - z^2) - 1)), or KB I0(gamma sqrt(1 - z^2)) / I0(gamma) (Eq. kb_compact
+// normalised to 1 at the centre)
+struct HostKernel {
+    int kind;
+    double shape;      // ES beta or KB gamma
+    double inv_norm;   // KB: 1 / I0(gamma)
+    double operator()(double z) const {
+        if (std::fabs(z) > 1.0) return 0.0;
+        const double r = std::sqrt(1.0 - z * z);
+        return kind == ENUFFT_KERNEL_KB ? std::cyl_bessel_i(0.0, shape * r) * inv_norm : std::exp(shape * (r - 1.0));
+    }
+};
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the Legendre recurrence)
 static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wts) {
@@ -164,27 +172,47 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 }
 
 // Phi(k) = integral of phi(2 tau / W) e^{-2 pi i k tau / nf} d tau (grid units), the kernel's
-// Fourier transform used by the deconvolution (Sec. 2.1.2, Eq. deconv)
-static double kernel_ft(int k, int W, int nf, double beta, const std::vector<double>& x,
+// Fourier transform used by the deconvolution (Sec. 2.1.2, Eq. deconv).  ES: Gauss-Legendre
+// quadrature.  KB: Eq. kb_fourier with a = W/2 and a k-independent factor 1/I0(gamma) in place of
+// 1/I0(beta) (the normalisation of the kernel): 2a sinh(s)/s, s = sqrt(gamma^2 - (a omega)^2),
+// omega = 2 pi k / nf, continued as 2a sin(s')/s', s' = sqrt((a omega)^2 - gamma^2), beyond gamma.
+static double kernel_ft(int k, int W, int nf, const HostKernel& ker, const std::vector<double>& x,
                         const std::vector<double>& wts) {
     const double pi = 3.14159265358979323846;
+    if (ker.kind == ENUFFT_KERNEL_KB) {
+        const double a = 0.5 * W, ao = a * 2.0 * pi * k / nf;
+        const double d = ker.shape * ker.shape - ao * ao;
+        double f;
+        if (d > 0.0) {
+            const double r = std::sqrt(d);
+            f = std::sinh(r) / r;
+        } else if (d < 0.0) {
+            const double r = std::sqrt(-d);
+            f = std::sin(r) / r;
+        } else {
+            f = 1.0;
+        }
+        return 2.0 * a * f * ker.inv_norm;
+    }
     double s = 0.0;
-    for (size_t i = 0; i < x.size(); ++i) s += wts[i] * es_kernel(x[i], beta) * std::cos(pi * k * W * x[i] / nf);
+    for (size_t i = 0; i < x.size(); ++i) s += wts[i] * ker(x[i]) * std::cos(pi * k * W * x[i] / nf);
     return 0.5 * W * s;
 }
 
 // Piece i of the kernel as a function of t in [0, 1): phi((t - W/2 + i) 2 / W); fit on
 // u = 2t - 1 by Chebyshev interpolation with `deg` coefficients, returned as monomials in u.
-static double fit_pieces(int W, double beta, int deg, KernelPoly& kp) {
+static double fit_pieces(int W, const HostKernel& ker, int deg, KernelPoly& kp) {
     const double pi = 3.14159265358979323846;
     kp.w = W;
     kp.deg = deg;
-    kp.beta = (float)beta;
+    kp.beta = (float)ker.shape;
+    kp.kind = ker.kind;
+    kp.inv_norm = ker.inv_norm;
     for (int i = 0; i < kMaxW; ++i)
         for (int d = 0; d < kMaxDeg; ++d) kp.c[i][d] = 0.0f;
     double maxerr = 0.0;
     for (int i = 0; i < W; ++i) {
-        auto f = [&](double u) { return es_kernel(((u + 1.0) * 0.5 - 0.5 * W + i) * 2.0 / W, beta); };
+        auto f = [&](double u) { return ker(((u + 1.0) * 0.5 - 0.5 * W + i) * 2.0 / W); };
         std::vector<double> a(deg, 0.0), fk(deg);
         for (int k = 0; k < deg; ++k) fk[k] = f(std::cos(pi * (k + 0.5) / deg));
         for (int j = 0; j < deg; ++j) {
@@ -233,6 +261,7 @@ void enufft_default_opts(enufft_opts* o) {
     o->mask = ENUFFT_MASK_CELL;
     o->eta = 1.5;
     o->tc_max_points = 0;
+    o->kernel = ENUFFT_KERNEL_ES;
 }
 
 void enufft_default_ems(enufft_ems_params* p) {
@@ -300,6 +329,8 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     if (!(o.eta > 0.0)) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: eta must be positive");
     if (o.tol < 0.0 || o.tol >= 1.0) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: tol must be in [0, 1)");
     if (o.tc_max_points < 0) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: tc_max_points < 0");
+    if (o.kernel != ENUFFT_KERNEL_ES && o.kernel != ENUFFT_KERNEL_KB)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad kernel");
 
     enufft_plan p = new enufft_plan_s();
     p->opts = o;
@@ -325,8 +356,18 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     p->W = W;
     p->NF = NF;
     p->sigma_eff = (double)NF / o.modes;
-    // ES shape: beta = 2.30 W at sigma = 2, scaled by (1 - 1/(2 sigma)) for other sigma
-    p->beta = 2.30 * W * (1.0 - 0.5 / p->sigma_eff) / 0.75;
+    HostKernel ker = {o.kernel, 0.0, 1.0};
+    if (o.kernel == ENUFFT_KERNEL_KB) {
+        // KB shape of Eq. kaisal_bessel_coeffs: beta = 2.34, gamma = pi sqrt((2 a beta / pi)^2 - 0.8),
+        // half-width a = W / 2 grid points
+        const double pi = 3.14159265358979323846, bkb = 2.34, t = W * bkb / pi;
+        ker.shape = pi * std::sqrt(t * t - 0.8);
+        ker.inv_norm = 1.0 / std::cyl_bessel_i(0.0, ker.shape);
+    } else {
+        // ES shape: beta = 2.30 W at sigma = 2, scaled by (1 - 1/(2 sigma)) for other sigma
+        ker.shape = 2.30 * W * (1.0 - 0.5 / p->sigma_eff) / 0.75;
+    }
+    p->beta = ker.shape;
     p->plain = o.prec == ENUFFT_FP32;
     if (p->plain && NF > 256) {
         enufft_plan_destroy(p);
@@ -344,15 +385,17 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         return fail(nullptr, ENUFFT_ERR_UNSUPPORTED, buf);
     }
     if (!p->dbl) {
-        p->poly_err = fit_pieces(W, p->beta, poly_deg(W), p->poly);
+        p->poly_err = fit_pieces(W, ker, poly_deg(W), p->poly);
     } else {
         p->poly.w = W;
         p->poly.beta = (float)p->beta;
+        p->poly.kind = ker.kind;
+        p->poly.inv_norm = ker.inv_norm;
     }
     {
         std::vector<double> gx, gw;
         gauss_legendre(256, gx, gw);
-        for (int k = 0; k <= p->P / 2; ++k) p->inv_phi[k] = 1.0 / kernel_ft(k, W, NF, p->beta, gx, gw);
+        for (int k = 0; k <= p->P / 2; ++k) p->inv_phi[k] = 1.0 / kernel_ft(k, W, NF, ker, gx, gw);
     }
 
     // device state
@@ -556,6 +599,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->cells_large = p->large ? p->n_cells : 0;
     info->precision = (int)p->opts.prec;
     info->cells_plain = p->plain ? p->n_cells : 0;
+    info->kernel = (int)p->opts.kernel;
     int64_t k = 0;
     if (p->plain) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
@@ -718,6 +762,8 @@ static enufft_status run_type1_plain(enufft_plan p, const void* x, const void* y
     r.W = p->W;
     r.P = p->P;
     r.beta = (float)p->beta;
+    r.kind = p->poly.kind;
+    r.inv_norm = (float)p->poly.inv_norm;
     r.inv_phi = p->inv_phi;
     r.twiddle = (const cplx<float>*)p->d_twiddle;
     r.grid = p->d_pgrid;

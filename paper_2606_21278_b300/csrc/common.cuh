@@ -73,11 +73,22 @@ constexpr int kMaxW = 16;
 constexpr int kMaxDeg = 16;
 // monomial coefficients per kernel piece used for width W (binary32 Horner evaluation)
 __host__ __device__ constexpr int poly_deg(int W) { return W + 2 < kMaxDeg ? W + 2 : kMaxDeg; }
+constexpr int KERNEL_ES = 0;   // exponential of semicircle
+constexpr int KERNEL_KB = 1;   // Kaiser-Bessel (Eq. kb_compact), normalised to 1 at the centre
 struct KernelPoly {
     int w;            // kernel width (grid points)
     int deg;          // number of monomial coefficients per piece
-    float beta;       // ES shape parameter
+    float beta;       // shape parameter (ES beta, KB gamma)
+    int kind;         // KERNEL_ES or KERNEL_KB
+    double inv_norm;  // KB: 1 / I0(gamma), the normalisation to phi(0) = 1
     float c[kMaxW][kMaxDeg];   // piece i: phi_i(u) = sum_d c[i][d] u^d, u = 2 t - 1, t in [0, 1)
 };
+
+// kernel value at z in [-1, 1] (binary64): the ES exp(beta (sqrt(1 - z^2) - 1)) or the KB
+// I0(gamma sqrt(1 - z^2)) / I0(gamma); shape is beta or gamma
+__device__ __forceinline__ double kernel_value_f64(const KernelPoly& kp, double shape, double z) {
+    const double r = sqrt(fmax(0.0, 1.0 - z * z));
+    return kp.kind == KERNEL_KB ? cyl_bessel_i0(shape * r) * kp.inv_norm : exp(shape * (r - 1.0));
+}
 
 }  // namespace enufft

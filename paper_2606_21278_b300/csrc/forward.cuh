@@ -180,10 +180,10 @@ __device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __re
     return true;
 }
 
-// binary64 path: window in binary64, direct kernel evaluation exp(beta (sqrt(1 - z^2) - 1))
+// binary64 path: window in binary64, direct kernel evaluation (ES or KB, binary64)
 template <int NF, int W>
-__device__ __forceinline__ bool prep_f64(const CellConst& cc, double beta, double px, double py, int& r0x,
-                                         int& r0y, double (&kx)[W], double (&ky)[W], unsigned* status) {
+__device__ __forceinline__ bool prep_f64(const CellConst& cc, const KernelPoly& kp, double beta, double px, double py,
+                                         int& r0x, int& r0y, double (&kx)[W], double (&ky)[W], unsigned* status) {
     if (!(isfinite(px) && isfinite(py))) {
         atomicOr(status, ST_NONFINITE);
         return false;
@@ -196,8 +196,8 @@ __device__ __forceinline__ bool prep_f64(const CellConst& cc, double beta, doubl
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         const double zx = ((double)(r0x + i) - sx) * (2.0 / W), zy = ((double)(r0y + i) - sy) * (2.0 / W);
-        kx[i] = exp(beta * (sqrt(fmax(0.0, 1.0 - zx * zx)) - 1.0));
-        ky[i] = exp(beta * (sqrt(fmax(0.0, 1.0 - zy * zy)) - 1.0));
+        kx[i] = kernel_value_f64(kp, beta, zx);
+        ky[i] = kernel_value_f64(kp, beta, zy);
     }
     return true;
 }
@@ -241,11 +241,11 @@ __device__ __forceinline__ void spread_f32(int* __restrict__ g, const FastFrame&
 
 // spread one sample (binary64 path)
 template <int NF, int W, int GS, int HO>
-__device__ __forceinline__ void spread_f64(double* __restrict__ g, const CellConst& cc, double beta,
-                                           double px, double py, double ph, double pw, unsigned* status) {
+__device__ __forceinline__ void spread_f64(double* __restrict__ g, const CellConst& cc, const KernelPoly& kp,
+                                           double beta, double px, double py, double ph, double pw, unsigned* status) {
     int r0x, r0y;
     double kx[W], ky[W];
-    if (!prep_f64<NF, W>(cc, beta, px, py, r0x, r0y, kx, ky, status)) return;
+    if (!prep_f64<NF, W>(cc, kp, beta, px, py, r0x, r0y, kx, ky, status)) return;
     const double c = pw * ph / cc.area;
     if (!isfinite(c)) {
         atomicOr(status, ST_NONFINITE);
@@ -391,7 +391,8 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
                 }
             } else {
                 for (; q < q1; q += CF::NT)
-                    spread_f64<NF, W, GS, HO>(sgrid, cc, a.beta, a.x[q], a.y[q], a.h[q], a.w[q], a.status);
+                    spread_f64<NF, W, GS, HO>(sgrid, cc, a.poly, a.beta, a.x[q], a.y[q], a.h[q], a.w[q],
+                                              a.status);
             }
         } else if (tid == 0) {
             atomicOr(a.status, ST_BADCELL);

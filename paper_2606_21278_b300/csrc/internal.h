@@ -37,7 +37,9 @@ struct PlainRun {
     int64_t n_cells;
     const CellConst* cells;
     int NF, W, P;
-    float beta;
+    float beta;                    // kernel shape (ES beta or KB gamma)
+    int kind;                      // KERNEL_ES or KERNEL_KB
+    float inv_norm;                // KB: 1 / I0(gamma)
     const double* inv_phi;         // host, P/2 + 1 entries
     const cplx<float>* twiddle;    // device, W_NF^j
     float* grid;                   // device scratch, NF * NF

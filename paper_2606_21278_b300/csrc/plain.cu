@@ -12,11 +12,18 @@
 
 namespace enufft {
 
+// kernel value at z in [-1, 1] in binary32 library calls: ES exp(beta (sqrt(1 - z^2) - 1)) or KB
+// I0(gamma sqrt(1 - z^2)) / I0(gamma)
+__device__ __forceinline__ float plain_kernel(int kind, float shape, float inv_norm, float z) {
+    const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    return kind == KERNEL_KB ? cyl_bessel_i0f(shape * r) * inv_norm : expf(shape * (r - 1.0f));
+}
+
 static __global__ void __launch_bounds__(256) plain_spread_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                                   const float* __restrict__ h, const float* __restrict__ w,
                                                                   int64_t q0, int64_t q1, const CellConst* __restrict__ cells,
-                                                                  int cell, int NF, int W, float beta, float* grid,
-                                                                  unsigned* status) {
+                                                                  int cell, int NF, int W, float beta, int kind,
+                                                                  float inv_norm, float* grid, unsigned* status) {
     const CellConst& cc = cells[cell];
     const int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= q1 || !cc.valid) return;
@@ -41,11 +48,11 @@ static __global__ void __launch_bounds__(256) plain_spread_kernel(const float* _
     float kx[kMaxW];
     for (int i = 0; i < W; ++i) {
         const float z = ((float)(r0x + i) - sx) * zs;
-        kx[i] = expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - z * z)) - 1.0f));
+        kx[i] = plain_kernel(kind, beta, inv_norm, z);
     }
     for (int j = 0; j < W; ++j) {
         const float z = ((float)(r0y + j) - sy) * zs;
-        const float cy = c * expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - z * z)) - 1.0f));
+        const float cy = c * plain_kernel(kind, beta, inv_norm, z);
         float* row = grid + (size_t)((r0y + j) & (NF - 1)) * NF;
         for (int i = 0; i < W; ++i) atomicAdd(row + ((r0x + i) & (NF - 1)), cy * kx[i]);
     }
@@ -114,7 +121,8 @@ cudaError_t plain_run(const PlainRun& r, cudaStream_t s) {
         const int64_t q0 = r.h_off[j], q1 = r.h_off[j + 1];
         if (q1 > q0)
             plain_spread_kernel<<<(unsigned)((q1 - q0 + 255) / 256), 256, 0, s>>>(r.x, r.y, r.h, r.w, q0, q1, r.cells, (int)j,
-                                                                                  r.NF, r.W, r.beta, r.grid, r.status);
+                                                                                  r.NF, r.W, r.beta, r.kind, r.inv_norm, r.grid,
+                                                                                  r.status);
         plain_fft_rows_kernel<<<r.NF, fthreads, smem, s>>>(r.grid, r.buf, r.twiddle, r.NF, lg);
         plain_fft_cols_kernel<<<r.P, fthreads, smem, s>>>(r.buf, r.twiddle, r.NF, lg, r.P);
         plain_deconv_kernel<<<(r.P * r.P + 255) / 256, 256, 0, s>>>(r.buf, r.NF, r.P, inv,
