@@ -36,18 +36,18 @@ def lib():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         d, i64, i32, vp = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-        _lib.oracle_frame.argtypes = [i32, vp, d, i32, vp]
-        _lib.oracle_window.argtypes = [i32, vp, d, i32, i64, vp, vp, vp]
-        _lib.oracle_type1_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, i32]
-        _lib.oracle_type1_backward_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp,
+        _lib.oracle_frame.argtypes = [i32, vp, d, i32, i32, vp]
+        _lib.oracle_window.argtypes = [i32, vp, d, i32, i32, i64, vp, vp, vp]
+        _lib.oracle_type1_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, i32, vp, i32]
+        _lib.oracle_type1_backward_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, i32, vp,
                                                      vp, vp, i32]
         _lib.oracle_ems_batch.argtypes = [i64, i32, vp, vp, i32, i32, i32, d, d, d, d, d, i32, i32, i32, d,
                                           vp, vp, vp, vp, i32]
         _lib.oracle_ems_energies.argtypes = [i32, vp, i32, i32, d, d, d, d, d, i32, d, vp, vp, vp, vp]
         _lib.oracle_ems_grad_coeffs.argtypes = [i64, i32, vp, vp, i32, i32, vp, vp, vp, vp]
         _lib.oracle_voronoi_weights_f32.argtypes = [i64, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, i32]
-        _lib.oracle_reconstruct_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp,
-                                                  vp, i32]
+        _lib.oracle_reconstruct_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32, i32, vp, vp,
+                                                  vp, vp, i32]
         for f in ("oracle_frame", "oracle_window", "oracle_type1_batch", "oracle_type1_backward_batch",
                   "oracle_ems_batch", "oracle_ems_energies", "oracle_ems_grad_coeffs",
                   "oracle_threads_used", "oracle_reconstruct_batch", "oracle_voronoi_weights_f32"):
@@ -87,18 +87,23 @@ class EMSParams:
                              # coefficient gate: an energy is a sum of squared moduli)
 
 
-def frame(nverts: int, verts, eta: float = 1.5, mask: int = 0) -> dict:
-    out = np.zeros(5)
+def frame(nverts: int, verts, eta: float = 1.5, mask: int = 0, frame: int = 0) -> dict:
+    """App. A frame of one cell (frame 0 centroid-aligned, 1 edge-aligned): centroid, H, L, |D|, the
+    rotation (cos t, sin t) and the vertices in the local frame u = R (x - x-bar)."""
+    out = np.zeros(19)
     v = _f64(verts).reshape(-1)
-    assert lib().oracle_frame(int(nverts), _p(v), float(eta), int(mask), _p(out)) == 0
-    return dict(cx=out[0], cy=out[1], H=out[2], L=out[3], area=out[4])
+    assert lib().oracle_frame(int(nverts), _p(v), float(eta), int(mask), int(frame), _p(out)) == 0
+    n = int(nverts)
+    return dict(cx=out[0], cy=out[1], H=out[2], L=out[3], area=out[4], cos=out[5], sin=out[6],
+                ux=out[7:7 + n].copy(), uy=out[13:13 + n].copy())
 
 
-def window(nverts: int, verts, x, y, eta: float = 1.5, mask: int = 0) -> np.ndarray:
+def window(nverts: int, verts, x, y, eta: float = 1.5, mask: int = 0, frame: int = 0) -> np.ndarray:
     v = _f64(verts).reshape(-1)
     x, y = _f64(x), _f64(y)
     win = np.zeros(len(x), dtype=np.int32)
-    assert lib().oracle_window(int(nverts), _p(v), float(eta), int(mask), len(x), _p(x), _p(y), _p(win)) == 0
+    assert lib().oracle_window(int(nverts), _p(v), float(eta), int(mask), int(frame), len(x), _p(x), _p(y),
+                               _p(win)) == 0
     return win
 
 
@@ -116,7 +121,7 @@ def type1(wl, nthreads: int = 0, P: int | None = None) -> np.ndarray:
     x, y, h, w = (_f64(a) for a in (wl.x, wl.y, wl.h, wl.w))
     out = np.zeros((len(nv), P, P, 2))
     r = lib().oracle_type1_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w), int(P),
-                                 float(wl.eta), int(wl.mask), _p(out), int(nthreads))
+                                 float(wl.eta), int(wl.mask), int(wl.frame), _p(out), int(nthreads))
     assert r == 0, "oracle_type1_batch failed"
     return out[..., 0] + 1j * out[..., 1]
 
@@ -133,7 +138,8 @@ def type1_backward(wl, G: np.ndarray, nthreads: int = 0):
     g = np.ascontiguousarray(np.stack([G.real, G.imag], -1), dtype=np.float64)
     gh = np.zeros(len(x)); gw = np.zeros(len(x))
     r = lib().oracle_type1_backward_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w),
-                                          int(P), float(wl.eta), int(wl.mask), _p(g), _p(gh), _p(gw),
+                                          int(P), float(wl.eta), int(wl.mask), int(wl.frame), _p(g), _p(gh),
+                                          _p(gw),
                                           int(nthreads))
     assert r == 0
     return gh, gw
@@ -141,7 +147,9 @@ def type1_backward(wl, G: np.ndarray, nthreads: int = 0):
 
 def voronoi_weights(wl, Ng: int = 64, nthreads: int = 0):
     """App. A Voronoi weights by raster sampling for binary32 samples: (w[n_points] float32,
-    counts[n_points] int32, -1 for samples outside their window); see oracle_voronoi_weights_f32."""
+    counts[n_points] int32, -1 for samples outside their window); see oracle_voronoi_weights_f32.
+    Centroid-aligned frame only."""
+    assert int(wl.frame) == 0, "Voronoi weights: centroid-aligned frame only"
     off, nv, vv = _cells(wl)
     x = np.ascontiguousarray(np.asarray(wl.x.cpu() if hasattr(wl.x, "cpu") else wl.x, dtype=np.float32))
     y = np.ascontiguousarray(np.asarray(wl.y.cpu() if hasattr(wl.y, "cpu") else wl.y, dtype=np.float32))
@@ -180,7 +188,8 @@ def reconstruct(wl, coeffs: np.ndarray, mask: np.ndarray, nthreads: int = 0):
     hrec = np.zeros(len(x))
     stats = np.zeros((len(nv), 4))
     r = lib().oracle_reconstruct_batch(len(nv), _p(off), _p(nv), _p(vv), _p(x), _p(y), _p(h), _p(w), int(P),
-                                       float(wl.eta), int(wl.mask), _p(c), _p(m), _p(hrec), _p(stats),
+                                       float(wl.eta), int(wl.mask), int(wl.frame), _p(c), _p(m), _p(hrec),
+                                       _p(stats),
                                        int(nthreads))
     assert r == 0, "oracle_reconstruct_batch failed"
     return hrec, stats

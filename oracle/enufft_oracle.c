@@ -6,8 +6,9 @@
  * baseline leg of the benchmark.  It shares no code, header, table or helper with the CUDA
  * library: every quantity is evaluated here directly from its definition.
  *
- *   frame       App. A  (centroid, centroid-aligned frame R = I, half-width H, square B,
- *                        shifted coordinates x' = u + H, masks D = B n {square, cell, circle})
+ *   frame       App. A  (centroid, centroid-aligned frame R = I or edge-aligned frame R of
+ *                        Eq. "rotation_matrix", centred coordinates u = R (x - x-bar), half-width H,
+ *                        square B, shifted coordinates x' = u + H, masks D = B n {square, cell, circle})
  *   |D|         App. A/B (area of the active quadrature domain)
  *   type-1      App. B, Eq. "discrete_quadrature":  h_mn = 1/|D| sum_q w_q h_q e^{-i(k_m x'_q + k_n y'_q)},
  *               k_m = 2 pi m / L, L = 2H, evaluated by direct summation (the NUFFT of Sec. 2.1.2 is a
@@ -52,11 +53,13 @@
 
 typedef struct {
     double cx, cy;   /* centroid x-bar                                  */
+    int edge;        /* 0: centroid-aligned frame (R = I); 1: edge-aligned frame           */
+    double rc, rs;   /* edge frame: R = [[rc, rs], [-rs, rc]], (rc, rs) = e_max / |e_max| */
     double H;        /* half-width of the square spectral domain B      */
     double L;        /* period L = 2H                                   */
     double area;     /* |D|, area of the active quadrature domain       */
     int nv;          /* polygon vertex count                            */
-    double ux[8], uy[8]; /* polygon vertices in the centred frame u = x - x-bar (R = I) */
+    double ux[8], uy[8]; /* polygon vertices in the local frame u = R (x - x-bar)          */
     double orient;   /* +1 counter-clockwise, -1 clockwise              */
     int mask;        /* 0 cell (B n polygon), 1 square (B), 2 circle (B n disk of radius H) */
 } oframe;
@@ -91,20 +94,48 @@ static int clip_halfplane(int n, const double *x, const double *y, int axis, dou
     return m;
 }
 
-/* Frame of one cell (App. A): centroid, centroid-aligned frame, H = (eta/2) max extent,
- * B = [-H, H]^2, and |D| for the chosen mask.  Returns 0, or -1 for a bad polygon. */
-static int frame_of(int nv, const double *v, double eta, int mask, oframe *f) {
-    if (nv < 3 || nv > 6) return -1;
+/* Local coordinates u = R (x - x-bar) of a point (App. A): R = I in the centroid-aligned frame;
+ * in the edge-aligned frame R = [[cos t, sin t], [-sin t, cos t]] (Eq. rotation_matrix). */
+static void local_of(const oframe *f, double x, double y, double *ux, double *uy) {
+    double dx = x - f->cx, dy = y - f->cy;
+    if (!f->edge) {
+        *ux = dx;
+        *uy = dy;
+    } else {
+        *ux = f->rc * dx + f->rs * dy;
+        *uy = -f->rs * dx + f->rc * dy;
+    }
+}
+
+/* Frame of one cell (App. A): centroid, orientation (frame 0: centroid-aligned, R = I; frame 1:
+ * edge-aligned, the longest edge e_i = v_(i+1) - v_i -- the first one on a tie -- made parallel to
+ * +x), H = (eta/2) max extent in that frame, B = [-H, H]^2, and |D| for the chosen mask.
+ * Returns 0, or -1 for a bad polygon or frame. */
+static int frame_of(int nv, const double *v, double eta, int mask, int frame, oframe *f) {
+    if (nv < 3 || nv > 6 || frame < 0 || frame > 1) return -1;
     memset(f, 0, sizeof(*f));
     f->nv = nv;
     f->mask = mask;
     for (int i = 0; i < nv; ++i) { f->cx += v[2 * i]; f->cy += v[2 * i + 1]; }
     f->cx /= nv;
     f->cy /= nv;
+    f->rc = 1.0;
+    if (frame == 1) {
+        double best = -1.0, ex = 1.0, ey = 0.0;
+        for (int i = 0; i < nv; ++i) {
+            int k = (i + 1) % nv;
+            double dx = v[2 * k] - v[2 * i], dy = v[2 * k + 1] - v[2 * i + 1];
+            double len = sqrt(dx * dx + dy * dy);
+            if (len > best) { best = len; ex = dx; ey = dy; }
+        }
+        if (!(best > 0.0)) return -1;
+        f->edge = 1;
+        f->rc = ex / best;   /* cos theta = e_x / |e_max| */
+        f->rs = ey / best;   /* sin theta = e_y / |e_max| */
+    }
     double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int i = 0; i < nv; ++i) {
-        f->ux[i] = v[2 * i] - f->cx;
-        f->uy[i] = v[2 * i + 1] - f->cy;
+        local_of(f, v[2 * i], v[2 * i + 1], &f->ux[i], &f->uy[i]);
         if (f->ux[i] < xmin) xmin = f->ux[i];
         if (f->ux[i] > xmax) xmax = f->ux[i];
         if (f->uy[i] < ymin) ymin = f->uy[i];
@@ -139,7 +170,8 @@ static int frame_of(int nv, const double *v, double eta, int mask, oframe *f) {
 
 /* Window indicator of a sample (App. A masks, closed sets). */
 static int in_window(const oframe *f, double x, double y) {
-    double ux = x - f->cx, uy = y - f->cy;
+    double ux, uy;
+    local_of(f, x, y, &ux, &uy);
     if (ux < -f->H || ux > f->H || uy < -f->H || uy > f->H) return 0; /* outside B */
     if (f->mask == 1) return 1;
     if (f->mask == 2) return ux * ux + uy * uy <= f->H * f->H;
@@ -151,19 +183,22 @@ static int in_window(const oframe *f, double x, double y) {
     return 1;
 }
 
-/* Exported: frame constants of one cell: out = {cx, cy, H, L, |D|}. */
-int oracle_frame(int nv, const double *verts, double eta, int mask, double *out) {
+/* Exported: frame constants of one cell: out = {cx, cy, H, L, |D|, cos t, sin t, u_x[0..5], u_y[0..5]}
+ * (19 doubles; the local vertices beyond nv are 0). */
+int oracle_frame(int nv, const double *verts, double eta, int mask, int frame, double *out) {
     oframe f;
-    if (frame_of(nv, verts, eta, mask, &f)) return -1;
+    if (frame_of(nv, verts, eta, mask, frame, &f)) return -1;
     out[0] = f.cx; out[1] = f.cy; out[2] = f.H; out[3] = f.L; out[4] = f.area;
+    out[5] = f.rc; out[6] = f.rs;
+    for (int i = 0; i < 6; ++i) { out[7 + i] = f.ux[i]; out[13 + i] = f.uy[i]; }
     return 0;
 }
 
 /* Exported: window indicator for Q samples of one cell. */
-int oracle_window(int nv, const double *verts, double eta, int mask, int64_t Q, const double *x,
+int oracle_window(int nv, const double *verts, double eta, int mask, int frame, int64_t Q, const double *x,
                   const double *y, int32_t *win) {
     oframe f;
-    if (frame_of(nv, verts, eta, mask, &f)) return -1;
+    if (frame_of(nv, verts, eta, mask, frame, &f)) return -1;
     for (int64_t q = 0; q < Q; ++q) win[q] = in_window(&f, x[q], y[q]);
     return 0;
 }
@@ -183,8 +218,10 @@ static int type1_cell(const oframe *f, int P, int64_t Q, const double *x, const 
     for (int64_t q = 0; q < Q; ++q) {
         if (!in_window(f, x[q], y[q])) continue;
         double c = w[q] * h[q] / f->area;             /* w_q h_q / |D| */
-        double xp = (x[q] - f->cx) + f->H;            /* x' = u_x + H  */
-        double yp = (y[q] - f->cy) + f->H;
+        double ux, uy;
+        local_of(f, x[q], y[q], &ux, &uy);
+        double xp = ux + f->H;                        /* x' = u_x + H  */
+        double yp = uy + f->H;
         for (int i = 0; i < P; ++i) {
             double k = 2.0 * ORACLE_PI * (double)(i - half) / f->L;   /* k_m = 2 pi m / L */
             ex[2 * i] = cos(k * xp);
@@ -212,7 +249,7 @@ static int nthreads_used = 1;
 /* Exported: batched type-1 over cells (CSR offsets), OpenMP over cells. */
 int oracle_type1_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
                        const double *verts /* n_cells * 12 */, const double *x, const double *y,
-                       const double *h, const double *w, int P, double eta, int mask,
+                       const double *h, const double *w, int P, double eta, int mask, int frame,
                        double *coeffs /* n_cells * P * P * 2 */, int nthreads) {
     int err = 0;
 #ifdef _OPENMP
@@ -222,7 +259,7 @@ int oracle_type1_batch(int64_t n_cells, const int64_t *offsets, const int32_t *n
 #endif
     for (int64_t j = 0; j < n_cells; ++j) {
         oframe f;
-        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, frame, &f)) { err |= 1; continue; }
         int64_t o = offsets[j], Q = offsets[j + 1] - offsets[j];
         if (type1_cell(&f, P, Q, x + o, y + o, h + o, w + o, coeffs + 2 * (size_t)P * P * j)) err |= 2;
     }
@@ -237,7 +274,9 @@ int oracle_threads_used(void) { return nthreads_used; }
 
 static double type2_point(const oframe *f, int P, const double *G, double xq, double yq) {
     int half = P / 2;
-    double xp = (xq - f->cx) + f->H, yp = (yq - f->cy) + f->H;
+    double ux, uy;
+    local_of(f, xq, yq, &ux, &uy);
+    double xp = ux + f->H, yp = uy + f->H;
     double acc = 0.0;
     for (int in = 0; in < P; ++in) {
         double kn = 2.0 * ORACLE_PI * (double)(in - half) / f->L;
@@ -256,7 +295,7 @@ static double type2_point(const oframe *f, int P, const double *G, double xq, do
  *   dL/dh_q = win_q w_q v_q / |D|,  dL/dw_q = win_q h_q v_q / |D|,  v_q = Re sum_mu G_mu e^{+i k.x'_q}. */
 int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
                                 const double *verts, const double *x, const double *y, const double *h,
-                                const double *w, int P, double eta, int mask, const double *G,
+                                const double *w, int P, double eta, int mask, int frame, const double *G,
                                 double *grad_h, double *grad_w, int nthreads) {
     int err = 0;
 #ifdef _OPENMP
@@ -265,7 +304,7 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
 #endif
     for (int64_t j = 0; j < n_cells; ++j) {
         oframe f;
-        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, frame, &f)) { err |= 1; continue; }
         const double *Gj = G + 2 * (size_t)P * P * j;
         for (int64_t q = offsets[j]; q < offsets[j + 1]; ++q) {
             if (!in_window(&f, x[q], y[q])) {
@@ -298,6 +337,7 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
 int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
                                const double *verts, const float *x, const float *y, double eta, int mask,
                                int Ng, float *w, int32_t *counts, int nthreads) {
+    const int frame = 0;   /* the raster of Eq. raster_grid is laid out in the centroid-aligned frame */
     int err = 0;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
@@ -306,7 +346,7 @@ int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const in
     for (int64_t j = 0; j < n_cells; ++j) {
         oframe f;
         const int64_t q0 = offsets[j], q1 = offsets[j + 1];
-        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) {
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, frame, &f)) {
             for (int64_t q = q0; q < q1; ++q) { w[q] = 0.0f; counts[q] = -1; }
             err |= 1;
             continue;
@@ -354,7 +394,7 @@ int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const in
  *   stats[4 j + 3] = sigma2_spec over the whole box, (m, n) != (0, 0)       (Eq. spectral_variance) */
 int oracle_reconstruct_batch(int64_t n_cells, const int64_t *offsets, const int32_t *nverts,
                              const double *verts, const double *x, const double *y, const double *h,
-                             const double *w, int P, double eta, int mask, const double *coeffs,
+                             const double *w, int P, double eta, int mask, int frame, const double *coeffs,
                              const uint8_t *modes, double *hrec, double *stats, int nthreads) {
     int err = 0;
 #ifdef _OPENMP
@@ -363,7 +403,7 @@ int oracle_reconstruct_batch(int64_t n_cells, const int64_t *offsets, const int3
 #endif
     for (int64_t j = 0; j < n_cells; ++j) {
         oframe f;
-        if (frame_of(nverts[j], verts + 12 * j, eta, mask, &f)) { err |= 1; continue; }
+        if (frame_of(nverts[j], verts + 12 * j, eta, mask, frame, &f)) { err |= 1; continue; }
         const double *cj = coeffs + 2 * (size_t)P * P * j;
         const uint8_t *sj = modes + (size_t)P * P * j;
         double *G = (double *)calloc(2 * (size_t)P * P, sizeof(double));

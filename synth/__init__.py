@@ -51,6 +51,7 @@ class Workload:
     eta: float = 1.5          # window expansion factor
     mask: int = 0             # 0 cell, 1 square, 2 circle
     tc_max_points: int = 0    # cells with Q <= this go to the tensor-core direct path (0 = off)
+    frame: int = 0            # 0 centroid-aligned, 1 edge-aligned local frame (App. A)
     meta: dict = field(default_factory=dict)
 
     @property

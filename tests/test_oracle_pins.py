@@ -529,3 +529,82 @@ def test_voronoi_weights_partition_the_window():
         inside = cnt[a:b] >= 0
         assert np.all(w[a:b][inside] > 0) and np.all(w[a:b][~inside] == 0)
     assert cnt[int(wl.offsets[1]) + 2] == -1
+
+
+# ---------------------------------------------------------------------------------------------
+# edge-aligned frame (App. A, Eq. rotation_matrix)
+# ---------------------------------------------------------------------------------------------
+
+def _one_cell(V, n=400, seed=0, frame=1, mask=0, P=16):
+    """One triangle V (3 x 2) with n uniform samples inside and a smooth field on them."""
+    rng = np.random.default_rng(seed)
+    r1, r2 = rng.random(n), rng.random(n)
+    flip = r1 + r2 > 1
+    r1[flip], r2[flip] = 1 - r1[flip], 1 - r2[flip]
+    P0, P1, P2 = (np.asarray(v, float) for v in V)
+    pts = P0 + r1[:, None] * (P1 - P0) + r2[:, None] * (P2 - P0)
+    h = np.cos(3 * pts[:, 0] + 1) + 0.5 * np.sin(2 * pts[:, 1] - 0.3) + 0.2
+    verts = torch.zeros(1, 6, 2, dtype=torch.float64)
+    verts[0, :3] = torch.tensor(np.asarray(V, float))
+    e1, e2 = P1 - P0, P2 - P0
+    area = 0.5 * abs(e1[0] * e2[1] - e1[1] * e2[0])
+    return synth.Workload(name="one_cell", n_cells=1, nverts=torch.tensor([3], dtype=torch.int32), verts=verts,
+                          offsets=torch.tensor([0, n]), x=torch.tensor(pts[:, 0]), y=torch.tensor(pts[:, 1]),
+                          h=torch.tensor(h), w=torch.full((n,), area / n, dtype=torch.float64), modes=P, eta=1.5,
+                          mask=mask, precision="fp64", frame=frame)
+
+
+def test_edge_frame_right_triangle_by_hand():
+    """Legs 4 (x) and 3 (y): the hypotenuse e2 = (-4, 3) is the longest edge, so cos t = -0.8,
+    sin t = 0.6; in the edge frame that edge is (5, 0), the extents are 5 (along it) and the height
+    12/5, hence H = eta/2 * 5, against eta/2 * 4 in the centroid frame; |D| is the triangle's area 6
+    (eta = 1.5 contains it) or L^2 for the square mask."""
+    V = np.array([[0.0, 0.0], [4.0, 0.0], [0.0, 3.0], [0, 0], [0, 0], [0, 0]])
+    fe = oracle.frame(3, V, 1.5, 0, frame=1)
+    fc = oracle.frame(3, V, 1.5, 0, frame=0)
+    assert abs(fe["cos"] + 0.8) < 1e-15 and abs(fe["sin"] - 0.6) < 1e-15
+    assert abs(fe["ux"][2] - fe["ux"][1] - 5.0) < 1e-14 and abs(fe["uy"][2] - fe["uy"][1]) < 1e-14
+    assert abs(np.ptp(fe["uy"]) - 2.4) < 1e-14
+    assert abs(fe["H"] - 0.75 * 5.0) < 1e-14 and abs(fc["H"] - 0.75 * 4.0) < 1e-14
+    assert abs(fe["area"] - 6.0) < 1e-13
+    assert abs(oracle.frame(3, V, 1.5, 1, frame=1)["area"] - (1.5 * 5.0) ** 2) < 1e-12
+
+
+def test_edge_frame_is_the_identity_when_the_longest_edge_points_along_x():
+    """Longest edge v1 -> v2 = (2, 0): R = I, so both frames give the same spectrum bit for bit."""
+    V = [[0.0, 0.0], [2.0, 0.0], [0.5, 1.0]]
+    c1 = oracle.type1(_one_cell(V, frame=1))
+    c0 = oracle.type1(_one_cell(V, frame=0))
+    assert np.array_equal(c1, c0)
+
+
+def test_edge_frame_half_turn_conjugates_the_spectrum():
+    """Longest edge v1 -> v2 = (-2, 0): R = -I, u -> -u and x' = -u + H, so for real h
+    h_mn(edge) = sum c e^{+i k.u} e^{-i k.H} = conj(h_mn(centroid)) e^{-2i(k_m + k_n) H}, and
+    (k_m + k_n) H = pi (m + n) makes the last factor 1: the edge-frame spectrum is the conjugate."""
+    V = [[2.0, 0.0], [0.0, 0.0], [0.5, 1.0]]
+    c1 = oracle.type1(_one_cell(V, frame=1))
+    c0 = oracle.type1(_one_cell(V, frame=0))
+    assert np.abs(c1 - np.conj(c0)).max() <= 1e-12 * np.abs(c0).max()
+
+
+@pytest.mark.parametrize("mask", [0, 1, 2])
+def test_edge_frame_is_attached_to_the_cell(mask):
+    """Rotating and translating the whole cell (vertices and samples) leaves the edge-frame spectrum
+    unchanged, for every mask, while the centroid-frame spectrum changes (a transposed or sign-flipped
+    R would turn the frame by twice the rotation and fail)."""
+    V = np.array([[0.1, -0.2], [1.3, 0.4], [0.2, 1.1]])
+    wl = _one_cell(V, mask=mask, seed=3)
+    a = 0.7
+    Rm = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    shift = np.array([3.0, -2.0])
+    V2 = V @ Rm.T + shift
+    wl2 = _one_cell(V2, mask=mask, seed=3)
+    pts = np.stack([wl.x.numpy(), wl.y.numpy()], 1) @ Rm.T + shift
+    wl2.x, wl2.y = torch.tensor(pts[:, 0]), torch.tensor(pts[:, 1])
+    wl2.h = wl.h.clone()
+    c, c2 = oracle.type1(wl), oracle.type1(wl2)
+    assert np.abs(c - c2).max() <= 1e-10 * np.abs(c).max()
+    wl.frame = wl2.frame = 0
+    d, d2 = oracle.type1(wl), oracle.type1(wl2)
+    assert np.abs(d - d2).max() > 1e-3 * np.abs(d).max()
