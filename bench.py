@@ -166,6 +166,7 @@ def _workload(args, seed, device):
         wl = wl.truncated(args.max_q)
     if args.tc_max_points is not None:
         wl.tc_max_points = args.tc_max_points
+    wl.frame = 1 if getattr(args, "frame", "centroid") == "edge" else 0
     return wl
 
 
@@ -222,7 +223,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = _workload(args, seed=rank, device="cuda")
-    plan = enufft.Plan.for_workload(wl, kernel=args.kernel)
+    plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame)
     info = plan.info()
     prm = enufft.EMSParams()
     coeffs = plan.new_coeffs()
@@ -393,7 +394,8 @@ def run_ours(args):
     # speed-up the metric states; timed the same way, fewer steps
     plain = None
     if not args.no_plain:
-        pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0, kernel=args.kernel)
+        pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0, kernel=args.kernel,
+                                         frame=args.frame)
         pco = pplan.new_coeffs()
         lib.enufft_set_stream(pplan._h, ctypes.c_void_p(stream.cuda_stream))
 
@@ -435,7 +437,7 @@ def run_ours(args):
                            **({"q_scale": args.q_scale} if args.q_scale != 1.0 else {}),
                            **({"max_q": args.max_q} if args.max_q is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
-                           "kernel": args.kernel, "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
+                           "kernel": args.kernel, "frame": args.frame, "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
                            "l2": f"inputs larger than L2 ({16 * wl.n_points / 1e9:.2f} GB of samples per step)",
                            "parallelism": f"cells sharded, {ws} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu_base,
@@ -499,6 +501,8 @@ def main():
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
     ap.add_argument("--kernel", default="es", choices=["es", "kb"],
                     help="spreading kernel: exponential of semicircle (default) or Kaiser-Bessel")
+    ap.add_argument("--frame", default="centroid", choices=["centroid", "edge"],
+                    help="local frame of every cell: centroid-aligned (default) or edge-aligned")
     ap.add_argument("--error-vs-width", action="store_true",
                     help="print the rel-l2 error against the oracle for kernel widths 4..13 (single triangle) and exit")
     args = ap.parse_args()

@@ -72,6 +72,20 @@ typedef enum { ENUFFT_MASK_CELL = 0, ENUFFT_MASK_SQUARE = 1, ENUFFT_MASK_CIRCLE 
  *       from the closed form of Eq. kb_fourier. */
 typedef enum { ENUFFT_KERNEL_ES = 0, ENUFFT_KERNEL_KB = 1 } enufft_kernel;
 
+/* Orientation of each cell's local frame (App. A).  Both use the centroid x-bar as origin and the
+ * square B = [-H, H]^2, H = (eta/2) max extent measured in the frame, x' = u + H.
+ *   CENTROID: the original axes, u = x - x-bar.
+ *   EDGE:     u = R (x - x-bar) with R = [[cos t, sin t], [-sin t, cos t]] (Eq. rotation_matrix),
+ *             (cos t, sin t) = e / |e| for the longest polygon edge e = v_(i+1) - v_i (the first one
+ *             on a tie), so that edge runs along +x.  Each execution call then starts with one
+ *             extra kernel that writes every sample's local coordinates, in binary64 arithmetic,
+ *             into plan-owned scratch (n_points x 2 values of the plan's precision), taking the
+ *             window decision there on the exact binary64 coordinates; binary32 plans store the
+ *             rounded coordinates, moved by at most a few units in the last place toward the
+ *             centroid where rounding would otherwise carry a windowed sample across the window's
+ *             boundary.  enufft_voronoi_weights is not built for these plans. */
+typedef enum { ENUFFT_FRAME_CENTROID = 0, ENUFFT_FRAME_EDGE = 1 } enufft_frame;
+
 typedef struct {
     int modes;            /* P, retained modes per dimension: even, 2..128                       */
     double oversamp;      /* sigma >= 2: fine grid n_f = smallest power of two >= sigma * P      */
@@ -86,6 +100,7 @@ typedef struct {
                              Mixed-precision plans with modes <= 64 only: other plans with a
                              positive value return ENUFFT_ERR_UNSUPPORTED                       */
     enufft_kernel kernel; /* spreading kernel (default ES)                                       */
+    enufft_frame frame;   /* local frame orientation (default CENTROID)                          */
 } enufft_opts;
 
 typedef struct {
@@ -99,7 +114,7 @@ typedef struct {
 } enufft_ems_params;
 
 /* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path,
- * ES kernel. */
+ * ES kernel, centroid-aligned frame. */
 void enufft_default_opts(enufft_opts *opts);
 /* Defaults of the paper's EMS illustration (Sec. 2.2): K_min 1, K_max 12, alpha 0..0.7,
  * delta 0.02, w1 = w2 = 0.5, HEAD sums, DC excluded. */
@@ -269,6 +284,7 @@ typedef struct {
     int precision;
     int64_t cells_plain, kernels_per_type1_ems;
     int kernel;                        /* enufft_kernel of the plan                             */
+    int frame;                         /* enufft_frame of the plan                              */
 } enufft_plan_info;
 enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
 

@@ -20,6 +20,7 @@ _lib = None
 
 _PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
 _KERNEL = {"es": 0, "kb": 1}
+_FRAME = {"centroid": 0, "edge": 1}
 _MASK = {"cell": 0, "square": 1, "circle": 2}
 
 
@@ -30,7 +31,8 @@ class EnufftError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("oversamp", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("tol", ctypes.c_double), ("prec", ctypes.c_int), ("mask", ctypes.c_int),
-                ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("frame", ctypes.c_int)]
 
 
 class _Ems(ctypes.Structure):
@@ -45,7 +47,7 @@ class _Info(ctypes.Structure):
                 ("n_cells", ctypes.c_int64), ("n_points", ctypes.c_int64), ("cells_fused", ctypes.c_int64),
                 ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("frame", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -117,7 +119,8 @@ class Plan:
 
     def __init__(self, offsets: torch.Tensor, nverts: torch.Tensor, verts: torch.Tensor, modes: int = 64,
                  oversamp: float = 2.0, kernel_width: int = 7, tol: float = 0.0, precision: str = "mixed",
-                 mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0, kernel: str = "es"):
+                 mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0, kernel: str = "es",
+                 frame: str | int = "centroid"):
         self._lib = load_library()
         if not torch.cuda.is_available():
             raise EnufftError("no CUDA device")
@@ -132,8 +135,11 @@ class Plan:
         self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         if kernel not in _KERNEL:
             raise EnufftError(f"kernel must be one of {sorted(_KERNEL)}")
+        if isinstance(frame, str) and frame not in _FRAME:
+            raise EnufftError(f"frame must be one of {sorted(_FRAME)}")
         o = _Opts(modes, oversamp, kernel_width, tol, _PREC[precision],
-                  _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points, _KERNEL[kernel])
+                  _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points, _KERNEL[kernel],
+                  _FRAME[frame] if isinstance(frame, str) else int(frame))
         h = ctypes.c_void_p()
         st = self._lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), self.n_cells, _ptr(self.offsets),
                                           _ptr(self.nverts), _ptr(self.verts), _stream())
@@ -146,7 +152,7 @@ class Plan:
     def for_workload(cls, wl, **kw) -> "Plan":
         args = dict(modes=wl.modes, oversamp=wl.sigma, kernel_width=wl.width, tol=wl.tol,
                     precision="fp64" if wl.precision == "fp64" else "mixed", mask=wl.mask, eta=wl.eta,
-                    tc_max_points=wl.tc_max_points)
+                    tc_max_points=wl.tc_max_points, frame=int(getattr(wl, "frame", 0)))
         args.update(kw)
         return cls(wl.offsets, wl.nverts, wl.verts, **args)
 

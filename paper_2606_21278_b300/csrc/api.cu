@@ -104,6 +104,11 @@ struct enufft_plan_s {
     float4* d_lrec = nullptr;
     float* d_lgrid = nullptr;
     int lmax_cells = 0;
+    // edge-aligned frame: per-cell centroid and rotation, per-call local coordinates of the samples
+    bool edge = false;
+    FrameRot* d_rot = nullptr;
+    void* d_vx = nullptr;
+    void* d_vy = nullptr;
     // plain binary32 per-cell path
     bool plain = false;
     std::vector<int64_t> h_off;
@@ -262,6 +267,7 @@ void enufft_default_opts(enufft_opts* o) {
     o->eta = 1.5;
     o->tc_max_points = 0;
     o->kernel = ENUFFT_KERNEL_ES;
+    o->frame = ENUFFT_FRAME_CENTROID;
 }
 
 void enufft_default_ems(enufft_ems_params* p) {
@@ -301,6 +307,9 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_lgrid);
     cudaFree(p->d_pgrid);
     cudaFree(p->d_pbuf);
+    cudaFree(p->d_rot);
+    cudaFree(p->d_vx);
+    cudaFree(p->d_vy);
     cudaSetDevice(cur);
     delete p;
     return ENUFFT_OK;
@@ -331,6 +340,8 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     if (o.tc_max_points < 0) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: tc_max_points < 0");
     if (o.kernel != ENUFFT_KERNEL_ES && o.kernel != ENUFFT_KERNEL_KB)
         return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad kernel");
+    if (o.frame != ENUFFT_FRAME_CENTROID && o.frame != ENUFFT_FRAME_EDGE)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad frame");
 
     enufft_plan p = new enufft_plan_s();
     p->opts = o;
@@ -470,9 +481,17 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->d_offsets, off.data(), sizeof(int64_t) * (n_cells + 1), cudaMemcpyHostToDevice,
                                 p->stream);
+        p->edge = o.frame == ENUFFT_FRAME_EDGE;
+        if (e == cudaSuccess && p->edge) {
+            const size_t vb = (size_t)std::max<int64_t>(p->n_points, 1) * (p->dbl ? 8 : 4);
+            e = cudaMalloc(&p->d_rot, sizeof(FrameRot) * n_cells);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->d_rot, 0, sizeof(FrameRot) * n_cells, p->stream);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_vx, vb);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_vy, vb);
+        }
         if (e == cudaSuccess) {
             frame_kernel<<<(unsigned)((n_cells + 127) / 128), 128, 0, p->stream>>>(
-                n_cells, d_cell_nverts, d_cell_verts, o.eta, (int)o.mask, NF, p->d_cells);
+                n_cells, d_cell_nverts, d_cell_verts, o.eta, (int)o.mask, NF, p->edge ? 1 : 0, p->d_cells, p->d_rot);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -600,6 +619,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->precision = (int)p->opts.prec;
     info->cells_plain = p->plain ? p->n_cells : 0;
     info->kernel = (int)p->opts.kernel;
+    info->frame = (int)p->opts.frame;
     int64_t k = 0;
     if (p->plain) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
@@ -610,6 +630,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     } else {
         k = (p->n_fused > 0) + (p->n_tc > 0) + 1;   // fused transform, tensor-core direct sum, EMS finish
     }
+    if (p->edge && p->n_points > 0) k += 1;   // local coordinates of the samples
     info->kernels_per_type1_ems = p->n_cells > 0 ? k : 0;
     return ENUFFT_OK;
 }
@@ -839,6 +860,19 @@ static enufft_status run_type1(enufft_plan p, const void* x, const void* y, cons
     return ENUFFT_OK;
 }
 
+// edge-aligned frame: the samples' local coordinates into plan scratch, and x, y pointed there
+static enufft_status edge_prepass(enufft_plan p, const void*& x, const void*& y) {
+    if (!p->edge || p->n_points == 0) return ENUFFT_OK;
+    // one wave of persistent blocks: three resident per SM (the kernel's launch bound)
+    const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 3);
+    cudaError_t e = launch_edge_frame(p->dbl, x, y, p->d_offsets, p->d_cells, p->d_rot, p->n_cells, p->d_vx, p->d_vy,
+                                      grid, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "edge frame: launch");
+    x = p->d_vx;
+    y = p->d_vy;
+    return ENUFFT_OK;
+}
+
 extern "C" {
 
 enufft_status enufft_type1(enufft_plan p, const void* d_x, const void* d_y, const void* d_h, const void* d_w,
@@ -849,6 +883,8 @@ enufft_status enufft_type1(enufft_plan p, const void* d_x, const void* d_y, cons
         return fail(p, ENUFFT_ERR_ARG, "type1: NULL data pointer");
     if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1: coeffs must be 16-byte aligned");
     cudaSetDevice(p->device);
+    const enufft_status es = edge_prepass(p, d_x, d_y);
+    if (es != ENUFFT_OK) return es;
     return p->dbl ? run_type1<double>(p, d_x, d_y, d_h, d_w, d_coeffs, nullptr)
                   : run_type1<float>(p, d_x, d_y, d_h, d_w, d_coeffs, nullptr);
 }
@@ -865,6 +901,8 @@ enufft_status enufft_type1_ems(enufft_plan p, const void* d_x, const void* d_y, 
         return fail(p, ENUFFT_ERR_ARG, "type1_ems: NULL data pointer");
     if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_ems: coeffs must be 16-byte aligned");
     cudaSetDevice(p->device);
+    st = edge_prepass(p, d_x, d_y);
+    if (st != ENUFFT_OK) return st;
     const EmsArgs ea = make_ems(prm, d_mode_weights, per_cell, d_kstar, d_sel, d_retained);
     return p->dbl ? run_type1<double>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea)
                   : run_type1<float>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea);
@@ -962,6 +1000,7 @@ extern "C" enufft_status enufft_voronoi_weights(enufft_plan p, const void* d_x, 
     if (p->n_cells == 0) return ENUFFT_OK;
     if (p->n_points > 0 && (!d_x || !d_y || !d_w)) return fail(p, ENUFFT_ERR_ARG, "voronoi_weights: NULL data pointer");
     if (p->dbl) return fail(p, ENUFFT_ERR_UNSUPPORTED, "voronoi_weights: binary32 samples only");
+    if (p->edge) return fail(p, ENUFFT_ERR_UNSUPPORTED, "voronoi_weights: not built for edge-frame plans");
     cudaSetDevice(p->device);
     cudaError_t e = launch_voronoi((const float*)d_x, (const float*)d_y, p->d_offsets, p->d_cells, (int)p->n_cells, ng,
                                    (float*)d_w, p->d_ctr + 2, p->num_sms, p->stream);
@@ -980,6 +1019,8 @@ extern "C" enufft_status enufft_reconstruct(enufft_plan p, const void* d_coeffs,
     if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for n_f = 256 plans");
     if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for plain FP32 plans");
     cudaSetDevice(p->device);
+    const enufft_status es = edge_prepass(p, d_x, d_y);
+    if (es != ENUFFT_OK) return es;
     return p->dbl ? run_reconstruct<double>(p, d_coeffs, d_kstar, d_sel, k_max, d_x, d_y, d_h, d_w, d_hrec, d_stats)
                   : run_reconstruct<float>(p, d_coeffs, d_kstar, d_sel, k_max, d_x, d_y, d_h, d_w, d_hrec, d_stats);
 }
@@ -995,6 +1036,8 @@ extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad
     if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for n_f = 256 plans");
     if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for plain FP32 plans");
     cudaSetDevice(p->device);
+    const enufft_status es = edge_prepass(p, d_x, d_y);
+    if (es != ENUFFT_OK) return es;
     return p->dbl ? run_adjoint<double>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w)
                   : run_adjoint<float>(p, d_grad_coeffs, d_x, d_y, d_h, d_w, d_grad_h, d_grad_w);
 }

@@ -10,6 +10,17 @@
 
 namespace enufft {
 
+// Edge-aligned frame (App. A, Eq. rotation_matrix): each cell's centroid and rotation, kept beside
+// its CellConst, whose frame is then the local one (origin 0, rotated vertices).
+struct FrameRot {
+    double cx, cy;   // centroid x-bar
+    double c, s;     // R = [[c, s], [-s, c]]
+};
+// Per-call pre-pass of edge-frame plans (edge_frame.cu): the local coordinates v = R (x - x-bar) of
+// every sample into (vx, vy), see enufft_frame.
+cudaError_t launch_edge_frame(bool dbl, const void* x, const void* y, const int64_t* offsets, const CellConst* cells,
+                              const FrameRot* rot, int64_t n_cells, void* vx, void* vy, int grid, cudaStream_t s);
+
 // Is (precision, n_f, W) compiled?  Shared-memory bytes and threads of the fused kernels.
 bool fused_supported(bool dbl, int nf, int w);
 size_t fused_smem_bytes(bool dbl, int nf, int w);

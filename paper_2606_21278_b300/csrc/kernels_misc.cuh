@@ -3,11 +3,14 @@
 
 #include "common.cuh"
 #include "ems.cuh"
+#include "internal.h"
 
 namespace enufft {
 
 // ---------------------------------------------------------------------------------------------
-// App. A frame of every cell, binary64: centroid, centroid-aligned frame (R = I),
+// App. A frame of every cell, binary64: centroid, centroid-aligned (R = I) or edge-aligned frame
+// (Eq. rotation_matrix: the longest edge made parallel to +x; its centroid and rotation go to rot[j]
+// and the cell's own constants describe the local frame, origin 0),
 // H = (eta / 2) max extent, L = 2H, |D| of the mask, plus the binary32 fast-path constants.
 // Centroid, extents, H, the centred vertices and the orientation follow the definition's
 // operation order exactly, because the binary64 window test decides boundary samples with them.
@@ -33,7 +36,8 @@ __device__ inline int clip_side(int n, const double* x, const double* y, int axi
 }
 
 static __global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__ nverts, const double* __restrict__ verts,
-                             double eta, int mask, int nf, CellConst* __restrict__ out) {
+                             double eta, int mask, int nf, int frame, CellConst* __restrict__ out,
+                             FrameRot* __restrict__ rot) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n_cells) return;
     CellConst cc;
@@ -53,10 +57,32 @@ static __global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__
     }
     cx = __ddiv_rn(cx, (double)nv);
     cy = __ddiv_rn(cy, (double)nv);
+    double rc = 1.0, rs = 0.0;
+    if (frame == 1) {
+        // longest edge e_i = v_(i+1) - v_i, the first on a tie; (cos t, sin t) = e / |e|
+        double best = -1.0, ex = 1.0, ey = 0.0;
+        for (int i = 0; i < nv; ++i) {
+            const int k = (i + 1) % nv;
+            const double dx = __dsub_rn(v[2 * k], v[2 * i]), dy = __dsub_rn(v[2 * k + 1], v[2 * i + 1]);
+            const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+            if (len > best) { best = len; ex = dx; ey = dy; }
+        }
+        if (best > 0.0) {
+            rc = __ddiv_rn(ex, best);
+            rs = __ddiv_rn(ey, best);
+        }
+        rot[j] = FrameRot{cx, cy, rc, rs};
+    }
     double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int i = 0; i < nv; ++i) {
-        cc.ux[i] = __dsub_rn(v[2 * i], cx);
-        cc.uy[i] = __dsub_rn(v[2 * i + 1], cy);
+        const double dx = __dsub_rn(v[2 * i], cx), dy = __dsub_rn(v[2 * i + 1], cy);
+        if (frame == 1) {   // u = R (x - x-bar)
+            cc.ux[i] = __dadd_rn(__dmul_rn(rc, dx), __dmul_rn(rs, dy));
+            cc.uy[i] = __dadd_rn(__dmul_rn(-rs, dx), __dmul_rn(rc, dy));
+        } else {
+            cc.ux[i] = dx;
+            cc.uy[i] = dy;
+        }
         xmin = fmin(xmin, cc.ux[i]); xmax = fmax(xmax, cc.ux[i]);
         ymin = fmin(ymin, cc.uy[i]); ymax = fmax(ymax, cc.uy[i]);
     }
@@ -69,6 +95,10 @@ static __global__ void frame_kernel(int64_t n_cells, const int32_t* __restrict__
         sa = __dadd_rn(sa, __dsub_rn(__dmul_rn(cc.ux[i], cc.uy[k]), __dmul_rn(cc.ux[k], cc.uy[i])));
     }
     cc.orient = sa >= 0.0 ? 1.0 : -1.0;
+    if (frame == 1) {   // the pre-pass hands every route local coordinates: origin 0
+        cx = 0.0;
+        cy = 0.0;
+    }
     cc.cx = cx;
     cc.cy = cy;
     cc.H = H;
