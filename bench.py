@@ -276,7 +276,9 @@ def run_ours(args):
     peak, peak_src = _peaks()
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(args.workload), "peak_source": peak_src, "kernel": (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish)" if info["cells_fused"]
+            "traffic": _traffic(args.workload) if args.frame == "centroid" else None, "peak_source": peak_src,
+            "kernel": (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish"
+                       + (", local-coordinate pre-pass)" if args.frame == "edge" else ")") if info["cells_fused"]
                                   else "n_f = 256 route, whole step (bin, scan, scatter, tile spread, FFT, EMS finish)"),
             "algorithmic_bytes_per_launch": alg_bytes}
 
@@ -430,7 +432,10 @@ def run_ours(args):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms,
+                "step_ms": {"median": float(np.median(launch_ms)), "best": float(np.min(launch_ms)),
+                            "mean": float(np.mean(launch_ms))},
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "n_cells": wl.n_cells, "n_points": wl.n_points, "modes": P,
                            "cells_tensor_core": info["cells_tensor"], "tc_max_points": wl.tc_max_points,
