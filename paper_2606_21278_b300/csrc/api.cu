@@ -102,7 +102,8 @@ struct enufft_plan_s {
     int* d_lblk_off = nullptr;       // [sort blocks of a batch][65] tile offsets
     float* d_lblk_abs = nullptr;     // [sort blocks of a batch][64] per-tile |c| sums
     float4* d_lrec = nullptr;
-    float* d_lgrid = nullptr;
+    unsigned long long* d_lgrid = nullptr;   // fixed-point fine grids of one batch
+    int* d_lexp = nullptr;                   // their scales
     int lmax_cells = 0;
     // edge-aligned frame: per-cell centroid and rotation, per-call local coordinates of the samples
     bool edge = false;
@@ -305,6 +306,7 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_lblk_abs);
     cudaFree(p->d_lrec);
     cudaFree(p->d_lgrid);
+    cudaFree(p->d_lexp);
     cudaFree(p->d_pgrid);
     cudaFree(p->d_pbuf);
     cudaFree(p->d_rot);
@@ -563,7 +565,8 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
             (e = cudaMalloc(&p->d_lblk_off, sizeof(int) * (kLTiles + 1) * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTiles * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_lgrid, sizeof(float) * kLNF * kLNF * mc)) != cudaSuccess) {
+            (e = cudaMalloc(&p->d_lgrid, sizeof(unsigned long long) * kLNF * kLNF * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lexp, sizeof(int) * mc)) != cudaSuccess) {
             enufft_status st = cuda_fail(nullptr, e, "plan_create: large-route scratch");
             enufft_plan_destroy(p);
             return st;
@@ -625,7 +628,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
         k += 2;   // EMS ranking + finish
     } else if (p->large) {
-        for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 3 : 2) : 0;   // sort, spread, FFT
+        for (const auto& b : p->lbatches) k += b.ncells > 0 ? (b.nblocks > 0 ? 4 : 3) : 0;   // sort, scale, spread, FFT
         k += 1;   // EMS finish
     } else {
         k = (p->n_fused > 0) + (p->n_tc > 0) + 1;   // fused transform, tensor-core direct sum, EMS finish
@@ -737,11 +740,13 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
     la.blk_abs = p->d_lblk_abs;
     la.rec = p->d_lrec;
     la.grid = p->d_lgrid;
+    la.cell_exp = p->d_lexp;
     la.status = p->d_ctr + 2;
     la.poly = p->poly;
     LargeFftArgs fa;
     memset(&fa, 0, sizeof(fa));
-    fa.grid = p->d_lgrid;
+    fa.grid = reinterpret_cast<const long long*>(p->d_lgrid);
+    fa.cell_exp = p->d_lexp;
     fa.P = p->P;
     fa.coeffs = (float*)coeffs;
     fa.twiddle = (const cplx<float>*)p->d_twiddle;
@@ -756,7 +761,8 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
         la.blocks = p->d_lblocks + b.block0;
         la.cell_blocks = p->d_lcellblk + b.cell0;
         la.work = p->d_lwork + b.work0;
-        cudaError_t e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(float) * kLNF * kLNF * (size_t)b.ncells, p->stream);
+        cudaError_t e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(unsigned long long) * kLNF * kLNF * (size_t)b.ncells,
+                                        p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): memset");
         e = large_run_batch(la, std::max(b.nblocks, 0), b.nwork, fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): launch");

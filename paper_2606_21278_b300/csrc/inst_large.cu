@@ -18,6 +18,8 @@ cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, con
                             int fft_grid, cudaStream_t s) {
     if (la.ncells <= 0) return cudaSuccess;
     if (nbin_blocks > 0) large_sort_kernel<<<nbin_blocks, kLSortThreads, 0, s>>>(la);
+    constexpr int cells_per_block = kLScaleThreads / 32;
+    large_scale_kernel<<<(la.ncells + cells_per_block - 1) / cells_per_block, kLScaleThreads, 0, s>>>(la);
     const int nt = nwork * kLTiles;
     switch (W) {
         case 4: launch_spread<4>(la, nt, s); break;

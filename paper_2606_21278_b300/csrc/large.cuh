@@ -10,7 +10,10 @@
 //               S = the sum of the item's sort blocks' per-tile sums bounds every node of its tile; each
 //               warp takes the tile's segment of one sort block at a time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
 //               point at the item's own scale 2^30 (1 - 2^-8) / S; the tile is then added to the
-//               cell's binary32 fine grid in global memory (periodic wrap) by red.global.add.f32;
+//               cell's fine grid in global memory (periodic wrap) in 64-bit fixed point at one scale
+//               per cell, 2^k with 2^61 / 2^k >= sum of the cell's per-tile sums (a bound of every
+//               node, taken in a fixed order by the scale kernel), by red.global.add.u64: integer adds
+//               do not depend on the order in which the tiles arrive, so reruns are bit-identical;
 //   3. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
 //               length 256), the P/2 + 1 needed columns in place, deconvolution/crop written as
 //               coalesced rows of the output, and the EMS ranking read straight from the
@@ -205,13 +208,45 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
         }
     }
     __syncthreads();
-    const float inv = 1.0f / scale;
-    float* g = a.grid + (size_t)cl * kLNF * kLNF;
+    // tile integers at this item's scale -> the cell's 64-bit fixed point: a binary32 product (the
+    // precision binary32 accumulation had), rounded to an integer; every value below 2^61
+    const float conv = (float)(ldexp(1.0, a.cell_exp[cl]) / (double)scale);
+    unsigned long long* g = a.grid + (size_t)cl * kLNF * kLNF;
     for (int i = tid; i < TC::TS * TC::TS; i += NT) {
         const int ly = i / TC::TS, lx = i % TC::TS;
         const int v = tile[ly * TC::TSTR + lx];
-        if (v) atomicAdd(g + ((ty0 + ly) & (kLNF - 1)) * kLNF + ((tx0 + lx) & (kLNF - 1)), (float)v * inv);
+        if (v)
+            atomicAdd(g + ((ty0 + ly) & (kLNF - 1)) * kLNF + ((tx0 + lx) & (kLNF - 1)),
+                      (unsigned long long)__float2ll_rn(__fmul_rn((float)v, conv)));
     }
+}
+
+// 3b. the scale of each batch cell's fixed-point grid: B = sum over its sort blocks and tiles of
+// the per-tile |c| sums, in a fixed order (lane-strided partial sums, then a fixed shuffle tree),
+// and k = 61 - e for B < 2^e, so the grid's integers stay below 2^61 (B is accurate to far better
+// than the factor 2 left to 2^62); one warp per cell
+constexpr int kLScaleThreads = 256;
+static __global__ void __launch_bounds__(kLScaleThreads) large_scale_kernel(const __grid_constant__ LargeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int cl = blockIdx.x * (kLScaleThreads / 32) + (threadIdx.x >> 5);
+    if (cl >= a.ncells) return;
+    const int2 cb = a.cell_blocks[cl];
+    float s = 0.0f;
+    for (int i = lane; i < cb.y * kLTiles; i += 32) s += a.blk_abs[(size_t)cb.x * kLTiles + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        int e = 0;
+        if (s > 0.0f && isfinite(s)) frexpf(s, &e);
+        a.cell_exp[cl] = 61 - e;
+    }
+}
+
+// fixed-point grid value -> binary32: the integer rounded to binary32, times 2^-k (fs, exact while
+// 2^-k is a normal binary32; outside that range the product is taken in binary64)
+__device__ __forceinline__ float large_grid_value(long long v, int k, float fs) {
+    if (k >= -126 && k <= 126) return __fmul_rn(__ll2float_rn(v), fs);
+    return (float)__dmul_rn(__ll2double_rn(v), ldexp(1.0, -k));
 }
 
 // 5. per-cell 256 x 256 FFT, deconvolution/crop, EMS ranking
@@ -246,14 +281,19 @@ static __global__ void __launch_bounds__(kLFftThreads) large_fft_kernel(const __
     for (int i = tid; i <= half; i += kLFftThreads) sinv[i] = a.inv_phi[i];
     for (int cl = blockIdx.x; cl < a.ncells; cl += gridDim.x) {
         const int cell = a.cell0 + cl;
-        const float* g = a.grid + (size_t)cl * kLNF * kLNF;
+        const long long* g = a.grid + (size_t)cl * kLNF * kLNF;
+        const int kexp = a.cell_exp[cl];
+        const float fs = (kexp >= -126 && kexp <= 126) ? __int_as_float((127 - kexp) << 23) : 0.0f;
         // ---- rows, in rounds of kLRowPairs pairs
         for (int rp0 = 0; rp0 < kLNF / 2; rp0 += kLRowPairs) {
             __syncthreads();
             for (int i = tid; i < 2 * kLRowPairs * (kLNF / 4); i += kLFftThreads) {
                 const int r = i / (kLNF / 4), c4 = i % (kLNF / 4);
-                const float4 v = reinterpret_cast<const float4*>(g + (size_t)(2 * rp0 + r) * kLNF)[c4];
-                reinterpret_cast<float4*>(rows + r * kLRowStride)[c4] = v;
+                const longlong2* src = reinterpret_cast<const longlong2*>(g + (size_t)(2 * rp0 + r) * kLNF) + 2 * c4;
+                const longlong2 u0 = src[0], u1 = src[1];
+                reinterpret_cast<float4*>(rows + r * kLRowStride)[c4] =
+                    make_float4(large_grid_value(u0.x, kexp, fs), large_grid_value(u0.y, kexp, fs),
+                                large_grid_value(u1.x, kexp, fs), large_grid_value(u1.y, kexp, fs));
             }
             __syncthreads();
             if (team < kLRowPairs) {

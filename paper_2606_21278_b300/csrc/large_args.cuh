@@ -30,7 +30,9 @@ struct LargeArgs {
     int* blk_off;                             // [sort block][kLTiles + 1]: tile offsets inside the block's range
     float* blk_abs;                           // [sort block][kLTiles]: sum |w h| / |D| of the block's samples per tile
     float4* rec;                              // [batch points] records {x, y, h, w}, tile-ordered per sort block
-    float* grid;                              // [ncells][256][256] binary32 fine grids
+    unsigned long long* grid;                 // [ncells][256][256] fine grids, 64-bit two's complement
+                                              // fixed point at the cell's scale 2^k (cell_exp)
+    int* cell_exp;                            // [ncells] k of each batch cell
     unsigned* status;
     KernelPoly poly;
 };
@@ -40,7 +42,8 @@ constexpr int kLRowStride = 272;              // >= 16 * 17 (team workspace), fl
 constexpr int kLRowPairs = 32;                // row pairs per round
 
 struct LargeFftArgs {
-    const float* __restrict__ grid;           // batch fine grids
+    const long long* __restrict__ grid;       // batch fine grids (fixed point, see LargeArgs)
+    const int* __restrict__ cell_exp;         // [ncells] their scales 2^k
     int cell0, ncells, P;
     float* __restrict__ coeffs;               // all cells
     const cplx<float>* __restrict__ twiddle;  // W_256^j

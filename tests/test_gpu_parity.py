@@ -289,8 +289,8 @@ def test_large_grid_route_matches_oracle():
     oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
     assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
     c2 = plan.type1(g.x, g.y, g.h, g.w)
-    # tile write-back adds binary32 values in a run-dependent order: reruns agree to rounding
-    assert _rel_l2(c2.cpu().numpy(), cn).max() <= 1e-6
+    # tiles are added to the fine grid in integer fixed point, so the arrival order does not matter
+    assert np.array_equal(c2.cpu().numpy(), cn)
 
 
 def test_large_grid_route_many_batches():
