@@ -5,7 +5,8 @@
 //               fine grid holding each sample's centre node, a counting sort by tile inside the
 //               block's own range of the record buffer (16-byte records {x, y, h, w}), the 65 tile
 //               offsets of the block and its per-tile sums of |w h| / |D|;
-//   2. spread   one block per (work item, tile), a work item being a cell or, for cells of more than
+//   2. scale    one warp per cell: the bound B of its fine grid's nodes and the grid's scale 2^k;
+//   3. spread   one block per (work item, tile), a work item being a cell or, for cells of more than
 //               2^18 samples, an interleaved part of its sort blocks (work items largest cell first):
 //               S = the sum of the item's sort blocks' per-tile sums bounds every node of its tile; each
 //               warp takes the tile's segment of one sort block at a time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
@@ -14,11 +15,11 @@
 //               per cell, 2^k with 2^61 / 2^k >= sum of the cell's per-tile sums (a bound of every
 //               node, taken in a fixed order by the scale kernel), by red.global.add.u64: integer adds
 //               do not depend on the order in which the tiles arrive, so reruns are bit-identical;
-//   3. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
+//   4. fft      one block per cell: row pairs through shared memory in rounds (team FFTs of
 //               length 256), the P/2 + 1 needed columns in place, deconvolution/crop written as
 //               coalesced rows of the output, and the EMS ranking read straight from the
 //               half spectrum.
-// The window test, the coordinates and the kernel of step 4 are those of the fused kernel
+// The window test, the coordinates and the kernel of step 3 are those of the fused kernel
 // (forward.cuh), so both routes compute the same sum.
 #pragma once
 
@@ -125,7 +126,7 @@ static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const 
     }
 }
 
-// 4. spread one (cell, tile): fixed point in shared memory, then added to the global fine grid
+// 3. spread one (cell, tile): fixed point in shared memory, then added to the global fine grid
 template <int W>
 struct LargeTileCfg {
     static constexpr int HS = W / 2 + 2;                   // halo per side
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
     }
 }
 
-// 3b. the scale of each batch cell's fixed-point grid: B = sum over its sort blocks and tiles of
+// 2. the scale of each batch cell's fixed-point grid: B = sum over its sort blocks and tiles of
 // the per-tile |c| sums, in a fixed order (lane-strided partial sums, then a fixed shuffle tree),
 // and k = 61 - e for B < 2^e, so the grid's integers stay below 2^61 (B is accurate to far better
 // than the factor 2 left to 2^62); one warp per cell
@@ -249,7 +250,7 @@ __device__ __forceinline__ float large_grid_value(long long v, int k, float fs) 
     return (float)__dmul_rn(__ll2double_rn(v), ldexp(1.0, -k));
 }
 
-// 5. per-cell 256 x 256 FFT, deconvolution/crop, EMS ranking
+// 4. per-cell 256 x 256 FFT, deconvolution/crop, EMS ranking
 // spectrum accessor on the half spectrum C1[k][m] (m = 0..P/2) with the deconvolution applied
 struct LargeHalfSpec {
     const cplx<float>* c1;
