@@ -279,7 +279,7 @@ def run_ours(args):
             "traffic": _traffic(args.workload) if args.frame == "centroid" else None, "peak_source": peak_src,
             "kernel": (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish"
                        + (", local-coordinate pre-pass)" if args.frame == "edge" else ")") if info["cells_fused"]
-                                  else "n_f = 256 route, whole step (bin, scan, scatter, tile spread, FFT, EMS finish)"),
+                                  else "n_f = 256 route, whole step (sort, scale, tile spread, FFT, EMS finish)"),
             "algorithmic_bytes_per_launch": alg_bytes}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
