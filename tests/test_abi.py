@@ -90,3 +90,19 @@ def test_null_arguments_are_errors(lib):
     assert lib.enufft_reconstruct(None, None, None, None, 12, None, None, None, None, None, None) == 1
     assert lib.enufft_voronoi_weights(None, None, None, 64, None) == 1
     assert lib.enufft_plan_destroy(None) == 0
+
+
+def test_binding_option_maps_match_the_header():
+    """The binding's option names map to the enum values that include/enufft.h declares."""
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "enufft.h")).read()
+    values = {name: int(v) for name, v in re.findall(r"\b(ENUFFT_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    expect = [
+        (enufft._PREC, {"fp64": "ENUFFT_FP64", "fp32": "ENUFFT_FP32", "mixed": "ENUFFT_MIXED"}),
+        (enufft._MASK, {"cell": "ENUFFT_MASK_CELL", "square": "ENUFFT_MASK_SQUARE", "circle": "ENUFFT_MASK_CIRCLE"}),
+        (enufft._KERNEL, {"es": "ENUFFT_KERNEL_ES", "kb": "ENUFFT_KERNEL_KB"}),
+        (enufft._FRAME, {"centroid": "ENUFFT_FRAME_CENTROID", "edge": "ENUFFT_FRAME_EDGE"}),
+    ]
+    for table, names in expect:
+        assert set(table) == set(names)
+        for key, cname in names.items():
+            assert table[key] == values[cname], (key, cname)
