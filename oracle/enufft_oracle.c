@@ -327,9 +327,9 @@ int oracle_type1_backward_batch(int64_t n_cells, const int64_t *offsets, const i
 /* Exported, for binary32 samples.  Per cell: raster points g_ab at the centres of an Ng x Ng grid
  * over B (Eq. raster_grid), X = (cx - H) + (L/Ng)(a + 1/2), Y = (cy - H) + (L/Ng)(b + 1/2) in binary64;
  * kept when in the window (Eq. raster_grid's subset G).  Each kept point goes to the nearest windowed
- * sample (Eq. nn_assignment); the decision is taken in binary32 -- X, Y rounded to binary32, then
- * d2 = (X - x_q)^2 + (Y - y_q)^2 with every operation rounded -- and a tie goes to the lowest sample
- * index.  n_q counts the points of sample q; A_q = n_q |D| / |G| (Eq. raster_area).  A windowed sample
+ * sample (Eq. nn_assignment), the squared distance d2 = (X - x_q)^2 + (Y - y_q)^2 taken in binary64
+ * (the samples' binary32 coordinates are exact in binary64), every operation rounded as written; a tie
+ * goes to the lowest sample index.  n_q counts the points of sample q; A_q = n_q |D| / |G| (Eq. raster_area).  A windowed sample
  * with n_q = 0 takes the floor n_q = 1/2 and all are renormalised to sum to |D| (Eq. area_partition),
  * so w_q = max(n_q, 1/2) (|D| / sum_q' max(n_q', 1/2)) in binary64, rounded once to binary32 (with
  * no empty cell this is A_q).  Samples outside the window, and samples with a non-finite
@@ -359,13 +359,12 @@ int oracle_voronoi_weights_f32(int64_t n_cells, const int64_t *offsets, const in
             for (int a2 = 0; a2 < Ng; ++a2) {
                 const double X = x0 + step * (a2 + 0.5), Y = y0 + step * (b + 0.5);
                 if (!in_window(&f, X, Y)) continue;
-                const float Xf = (float)X, Yf = (float)Y;
-                float best = 0.0f;
+                double best = 0.0;
                 int64_t arg = -1;
                 for (int64_t q = q0; q < q1; ++q) {
                     if (counts[q] < 0) continue;
-                    const float dx = Xf - x[q], dy = Yf - y[q];
-                    const float d2 = dx * dx + dy * dy;
+                    const double dx = X - (double)x[q], dy = Y - (double)y[q];
+                    const double d2 = dx * dx + dy * dy;
                     if (arg < 0 || d2 < best) { best = d2; arg = q; }
                 }
                 if (arg >= 0) counts[arg] += 1;

@@ -4,15 +4,18 @@
 //   1. the window decision of every sample (the same certified binary32 test with binary64
 //      fallback as the transform, so the windowed set is the transform's);
 //   2. the raster points g_ab = (cx - H + (L/Ng)(a + 1/2), cy - H + (L/Ng)(b + 1/2)) in binary64,
-//      kept when inside the window; each kept point is assigned to its nearest windowed sample,
-//      the squared distance taken in binary32 with every operation rounded as written, ties to the
-//      lowest sample index; the counts n_q are accumulated by integer atomics (in the output
-//      array, reinterpreted).  The search: the cell's windowed samples are sorted by a counting
-//      sort into a G x G grid of buckets over B in shared memory (about two per bucket), and each
-//      point examines rings of buckets around its own until its best distance is below
-//      0.999 r times the bucket width -- every sample not yet examined is then farther by more
-//      than binary32 rounding, so it can neither win nor tie; cells with more windowed samples
-//      than the shared-memory capacity are searched by brute force over tiles of the samples;
+//      kept when inside the window; each kept point is assigned to its nearest windowed sample
+//      (Eq. nn_assignment), ties to the lowest sample index; the counts n_q are accumulated by
+//      integer atomics (in the output array, reinterpreted).  The nearest sample is the one of
+//      the squared distances d2 = (X - x_q)^2 + (Y - y_q)^2 taken in binary64.  The search runs in
+//      binary32 first and keeps the best and the second-best distance; when the gap between them
+//      exceeds a certified bound of the binary32 rounding error (plus the binary64 one), the
+//      binary32 winner is the binary64 winner.  Otherwise the point is searched again with binary64
+//      distances in the definition's operation order.  The search: the cell's windowed samples are
+//      sorted by a counting sort into a G x G grid of buckets over B in shared memory (about two per
+//      bucket), and each point examines rings of buckets around its own until every sample not yet
+//      examined is certainly farther than its best one; cells with more windowed samples than the
+//      shared-memory capacity are searched by brute force over tiles of the samples;
 //   3. w_q = max(n_q, 1/2) |D| / sum_q' max(n_q', 1/2) in binary64, rounded to binary32 (the floor
 //      of 1/2 for a sample no raster point reached, then the renormalisation of Eq. area_partition);
 //      samples outside the window get 0.
@@ -31,12 +34,19 @@ constexpr size_t kVorSmem = (size_t)kVorCap * 12 + sizeof(int) * (kVorMaxG * kVo
 static_assert(kVorCap * 8 >= 2 * kVorTile * 4, "brute-force tiles fit in the sample area");
 }  // namespace
 
+// raster point idx of a cell in binary64 (Eq. raster_grid)
+__device__ __forceinline__ void vor_point_f64(double x0, double y0, double step, int Ng, int idx, double& Xd,
+                                              double& Yd) {
+    const int a = idx % Ng, b = idx / Ng;
+    Xd = __dadd_rn(x0, __dmul_rn(step, (double)a + 0.5));
+    Yd = __dadd_rn(y0, __dmul_rn(step, (double)b + 0.5));
+}
+
 // raster point idx of a cell: binary32 coordinates (INFINITY when outside the window)
 __device__ __forceinline__ void vor_point(const CellConst& cc, const FastFrame& ff, double x0, double y0, double step,
                                           int Ng, int idx, float& X, float& Y) {
-    const int a = idx % Ng, b = idx / Ng;
-    const double Xd = __dadd_rn(x0, __dmul_rn(step, (double)a + 0.5));
-    const double Yd = __dadd_rn(y0, __dmul_rn(step, (double)b + 0.5));
+    double Xd, Yd;
+    vor_point_f64(x0, y0, step, Ng, idx, Xd, Yd);
     int in = window_f32(ff, cc.edge, __double2float_rn(__dsub_rn(Xd, cc.cx)), __double2float_rn(__dsub_rn(Yd, cc.cy)));
     if (in < 0) in = window_f64(cc, Xd, Yd);
     X = in ? __double2float_rn(Xd) : INFINITY;
@@ -48,20 +58,49 @@ __device__ __forceinline__ float vor_d2(float X, float Y, float qx, float qy) {
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
 }
 
-// brute force over shared-memory tiles of the cell's samples (any cell size)
+// the definition's squared distance: binary64, every operation rounded as written
+__device__ __forceinline__ double vor_d2_f64(double X, double Y, float qx, float qy) {
+    const double dx = __dsub_rn(X, (double)qx), dy = __dsub_rn(Y, (double)qy);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+// Bound of |d2f - d2| for a binary32 distance d2f from the rounded raster point (A: the larger of
+// its coordinate magnitudes) to a binary32 sample, against the exact d2 from the binary64 point:
+// rounding the point moves it by at most u A, each of the four operations adds a relative u
+// (u = 2^-24), and the true distance s is at most sqrt(d2f) + 3 u A; taken with 50 % slack.
+__device__ __forceinline__ float vor_err32(float d2f, float A) {
+    constexpr float u = 0x1p-24f;
+    const float s = sqrtf(d2f) * 1.0001f + 3.0f * u * A;
+    return u * (5.0f * A * s + 8.0f * s * s) + 4.0f * u * u * A * A;
+}
+// Is the binary32 winner (best) certainly the binary64 winner?  Every other candidate has a binary32
+// distance >= second, and every sample not examined has an exact squared distance >= lb2.  The
+// exact distances then differ by more than the binary32 bounds; a gap of at least one binary32 ulp
+// (2^-24 relative) also exceeds the binary64 rounding (five roundings of 2^-53 on each side), so
+// the binary64 computation ranks the two the same way.
+__device__ __forceinline__ bool vor_certified(float best, float second, float lb2, float A) {
+    const float hi_best = best + vor_err32(best, A);
+    const float lo_second = second < INFINITY ? second - vor_err32(second, A) : INFINITY;
+    return fminf(lo_second, lb2) > hi_best;
+}
+
+// brute force over shared-memory tiles of the cell's samples (any cell size): binary32 distances
+// with the best and second-best per point, then one more pass in binary64 for the points whose
+// binary32 winner is not certified (taken by the whole block when any point needs it)
 __device__ void vor_brute(const float* __restrict__ x, const float* __restrict__ y, int64_t q0, int64_t q1,
                           const CellConst& cc, const FastFrame& ff, double x0, double y0, double step, int Ng, int* cnt,
                           float* sx, float* sy) {
     const int tid = threadIdx.x, nt_ = blockDim.x;
     const int npts = Ng * Ng;
     for (int base = 0; base < npts; base += nt_ * kVorR) {
-        float X[kVorR], Y[kVorR], best[kVorR];
+        float X[kVorR], Y[kVorR], best[kVorR], second[kVorR];
         int arg[kVorR];
 #pragma unroll
         for (int r = 0; r < kVorR; ++r) {
             const int idx = base + tid + nt_ * r;
             arg[r] = -1;
             best[r] = INFINITY;
+            second[r] = INFINITY;
             X[r] = INFINITY;   // points outside the window never take a sample
             Y[r] = INFINITY;
             if (idx < npts) vor_point(cc, ff, x0, y0, step, Ng, idx, X[r], Y[r]);
@@ -80,9 +119,50 @@ __device__ void vor_brute(const float* __restrict__ x, const float* __restrict__
 #pragma unroll
                 for (int r = 0; r < kVorR; ++r) {
                     const float d2 = vor_d2(X[r], Y[r], qx, qy);
-                    if (d2 < best[r]) {
+                    if (d2 < best[r]) {   // samples in index order: a tie keeps the lower index
+                        second[r] = best[r];
                         best[r] = d2;
                         arg[r] = (int)(t0 - q0) + i;
+                    } else if (d2 < second[r]) {
+                        second[r] = d2;
+                    }
+                }
+            }
+        }
+        bool need = false, f64[kVorR];
+#pragma unroll
+        for (int r = 0; r < kVorR; ++r) {
+            f64[r] = arg[r] >= 0 && !vor_certified(best[r], second[r], INFINITY, fmaxf(fabsf(X[r]), fabsf(Y[r])));
+            need |= f64[r];
+        }
+        if (__syncthreads_or(need)) {
+            double Xd[kVorR], Yd[kVorR], b64[kVorR];
+#pragma unroll
+            for (int r = 0; r < kVorR; ++r) {
+                vor_point_f64(x0, y0, step, Ng, base + tid + nt_ * r, Xd[r], Yd[r]);
+                b64[r] = INFINITY;
+            }
+            for (int64_t t0 = q0; t0 < q1; t0 += kVorTile) {
+                const int nt = (q1 - t0) < (int64_t)kVorTile ? (int)(q1 - t0) : kVorTile;
+                __syncthreads();
+                for (int i = tid; i < nt; i += nt_) {
+                    const bool in = cnt[t0 + i] >= 0;
+                    sx[i] = in ? x[t0 + i] : INFINITY;
+                    sy[i] = in ? y[t0 + i] : INFINITY;
+                }
+                __syncthreads();
+                if (need) {
+                    for (int i = 0; i < nt; ++i) {
+                        const float qx = sx[i], qy = sy[i];
+#pragma unroll
+                        for (int r = 0; r < kVorR; ++r) {
+                            if (!f64[r]) continue;
+                            const double d2 = vor_d2_f64(Xd[r], Yd[r], qx, qy);
+                            if (d2 < b64[r]) {   // index order: a tie keeps the lower index
+                                b64[r] = d2;
+                                arg[r] = (int)(t0 - q0) + i;
+                            }
+                        }
                     }
                 }
             }
@@ -238,12 +318,20 @@ static __global__ void __launch_bounds__(kVorThreads) voronoi_kernel(const float
                 int px = (int)((X - bx0) * ibw), py = (int)((Y - by0) * ibw);
                 px = px < 0 ? 0 : (px >= G ? G - 1 : px);
                 py = py < 0 ? 0 : (py >= G ? G - 1 : py);
-                float best = INFINITY;
+                const float A = fmaxf(fabsf(X), fabsf(Y));
+                float best = INFINITY, second = INFINITY, lb2 = INFINITY;
                 int arg = 0x7fffffff;
                 for (int r = 0; r <= G; ++r) {
                     // every sample not yet examined lies in a bucket at least r away by index, so at
-                    // least (r - 1) bucket widths from the point
-                    if (r > 1 && best < INFINITY && sqrtf(best) <= 0.999f * (float)(r - 1) * bw) break;
+                    // least (r - 1) bucket widths from the point: stop once that is certainly farther
+                    // than the best distance
+                    if (r > 1 && best < INFINITY) {
+                        const float lb = 0.999f * (float)(r - 1) * bw;
+                        if (lb * lb > best + vor_err32(best, A)) {
+                            lb2 = lb * lb;
+                            break;
+                        }
+                    }
                     for (int dy = -r; dy <= r; ++dy) {
                         const int by = py + dy;
                         if (by < 0 || by >= G) continue;
@@ -257,11 +345,48 @@ static __global__ void __launch_bounds__(kVorThreads) voronoi_kernel(const float
                                 const float d2 = vor_d2(X, Y, qv.x, qv.y);
                                 const int qi = bidx[s];
                                 if (d2 < best || (d2 == best && qi < arg)) {
+                                    second = best;
                                     best = d2;
                                     arg = qi;
+                                } else if (d2 < second) {
+                                    second = d2;
                                 }
                             }
                             if (r == 0) break;
+                        }
+                    }
+                }
+                if (arg != 0x7fffffff && !vor_certified(best, second, lb2, A)) {
+                    // the same search with the definition's binary64 distances; it stops once every
+                    // sample not examined is farther than the best by more than binary64 rounding
+                    double Xd, Yd;
+                    vor_point_f64(x0, y0, step, Ng, idx, Xd, Yd);
+                    double b64 = INFINITY;
+                    arg = 0x7fffffff;
+                    for (int r = 0; r <= G; ++r) {
+                        if (r > 1 && b64 < INFINITY) {
+                            const double lb = 0.999 * (double)(r - 1) * (double)bw;
+                            if (lb * lb * (1.0 - 0x1p-40) > b64) break;
+                        }
+                        for (int dy = -r; dy <= r; ++dy) {
+                            const int by = py + dy;
+                            if (by < 0 || by >= G) continue;
+                            const int stepx = (dy == -r || dy == r) ? 1 : 2 * r;
+                            for (int dx = -r; dx <= r; dx += (stepx > 0 ? stepx : 1)) {
+                                const int bx = px + dx;
+                                if (bx < 0 || bx >= G) continue;
+                                const int b = by * G + bx;
+                                for (int s = boff[b]; s < boff[b + 1]; ++s) {
+                                    const float2 qv = bxy[s];
+                                    const double d2 = vor_d2_f64(Xd, Yd, qv.x, qv.y);
+                                    const int qi = bidx[s];
+                                    if (d2 < b64 || (d2 == b64 && qi < arg)) {
+                                        b64 = d2;
+                                        arg = qi;
+                                    }
+                                }
+                                if (r == 0) break;
+                            }
                         }
                     }
                 }

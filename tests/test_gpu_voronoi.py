@@ -1,7 +1,8 @@
 """GPU parity of the Voronoi quadrature weights (enufft_voronoi_weights) against the oracle.  The
-nearest-sample decisions are integers taken from binary32 arithmetic on both sides in the same
-operation order, so the counts agree exactly; the weights then agree to the last bit (up to one unit
-of binary32 rounding through |D|)."""
+oracle takes each nearest-sample decision (App. A, Eq. nn_assignment) with binary64 distances; the
+kernel takes it in binary32 where the gap to the second-nearest sample exceeds a certified rounding
+bound and in binary64 otherwise, so the counts agree exactly; the weights then agree to the last bit
+(up to one unit of binary32 rounding through |D|)."""
 import numpy as np
 import pytest
 import torch
@@ -64,3 +65,37 @@ def test_voronoi_weights_feed_the_transform():
     cn = c.cpu().numpy()
     err = np.linalg.norm((cn - ref).reshape(4, -1), axis=1) / np.linalg.norm(ref.reshape(4, -1), axis=1)
     assert err.max() <= 1e-5, err
+
+
+def _square(xs, ys, half=0.5):
+    """One square cell [-half, half]^2 (window = the square) with the given binary32 samples."""
+    wl = synth.regular_grid_square_cell(1, lambda a, b: torch.zeros_like(a), half=half, dtype=torch.float32)
+    n = len(xs)
+    return synth.Workload(**{**wl.__dict__, "x": torch.tensor(xs, dtype=torch.float32),
+                             "y": torch.tensor(ys, dtype=torch.float32), "h": torch.ones(n, dtype=torch.float32),
+                             "w": torch.ones(n, dtype=torch.float32), "offsets": torch.tensor([0, n], dtype=torch.int64)})
+
+
+@pytest.mark.parametrize("extra", [0, 17000])   # bucketed search; brute force (> 16384 windowed samples)
+def test_voronoi_binary32_ties_are_decided_in_binary64(extra):
+    """On a raster column whose abscissa X is not a binary32 number, two samples symmetric about
+    binary32(X) tie in binary32 but not in binary64: the sample on X's side must own the column (the
+    first sample, on the other side, would win a binary32 tie).  With `extra` duplicate samples in the
+    far corner the cell takes the brute-force search."""
+    Ng, D = 10, 2.0 ** -7
+    fr = oracle.frame(4, _square([0.0], [0.0]).verts[0], 1.0, 1)
+    x0, y0, step = fr["cx"] - fr["H"], fr["cy"] - fr["H"], fr["L"] / Ng
+    a = next(a for a in range(Ng) if float(np.float32(x0 + step * (a + 0.5))) != x0 + step * (a + 0.5))
+    X = x0 + step * (a + 0.5)
+    Xf = float(np.float32(X))
+    near, far = (Xf + D, Xf - D) if X > Xf else (Xf - D, Xf + D)
+    Yf = float(np.float32(y0 + step * 3.5))
+    xs, ys = [far, near] + [0.49] * extra, [Yf, Yf] + [-0.49] * extra
+    wl = _square(xs, ys)
+    g = wl.to("cuda")
+    plan = enufft.Plan.for_workload(g)
+    w = plan.voronoi_weights(g.x, g.y, Ng).cpu().numpy()
+    plan.sync_status()
+    ow, cnt = oracle.voronoi_weights(wl, Ng)
+    assert _close(w, ow)
+    assert cnt[1] >= Ng   # the near sample owns column a (and every column on its side)

@@ -477,6 +477,42 @@ def test_reconstruction_from_no_modes():
     assert np.all(st[:, 3] > 0) and np.all(st[:, 1] > 0)
 
 
+def _setpair(c, m, n, amp):
+    P = c.shape[-1]
+    half = P // 2
+    c[0, n + half, m + half] = amp
+    c[0, -n + half, -m + half] = np.conj(amp)
+
+
+def test_mode_set_gate_separates_near_ties_from_errors():
+    """The end-to-end EMS mode-set gate: an identical spectrum passes with no mismatch; a selection that
+    differs from the oracle's while every energy agrees exactly is an error, not a near-tie; two head
+    energies 1e-9 apart, swapped by a 1e-8 relative change of one of them, are a near-tie whose measured
+    energy error is about 2e-8."""
+    rng = np.random.default_rng(4)
+    P = 16
+    c = 0.01 * (rng.standard_normal((1, P, P)) + 1j * rng.standard_normal((1, P, P)))
+    pos = [(m, n) for n in range(1, 5) for m in range(-3, 4)][:14]
+    for k, (m, n) in enumerate(pos):                  # a flat head: K* = 6 of 14 strong pairs
+        _setpair(c, m, n, 10.0 * (1 - 0.01 * k))
+    ks, sel, _, _ = oracle.ems(c)
+    assert ks[0] >= 3
+    g = oracle.mode_set_gate(c, ks, sel, c)
+    assert g["mismatches"] == [] and g["all_near_ties"]
+    sel2 = sel.copy()
+    sel2[0, 0] = (P // 2 + 6) * P + (P // 2 - 5)      # a background pair, far below the head
+    g = oracle.mode_set_gate(c, ks, sel2, c)
+    assert len(g["mismatches"]) == 1 and not g["all_near_ties"]
+    c3 = c.copy()
+    _setpair(c3, *pos[2], 10.0 * 0.99 * (1 - 1e-9))   # nearly ties with the second pair
+    c4 = c3.copy()
+    _setpair(c4, *pos[2], 10.0 * 0.99 * (1 - 1e-9) * (1 + 1e-8))
+    ks4, sel4, _, _ = oracle.ems(c4)
+    g = oracle.mode_set_gate(c4, ks4, sel4, c3)
+    assert len(g["mismatches"]) == 1 and g["all_near_ties"]
+    assert 1e-8 < g["mismatches"][0]["energy_err"] < 3e-8
+
+
 # ----------------------------------------------------------------------------------------------
 # Voronoi quadrature weights by raster sampling (App. A, Eqs. raster_grid .. voronoi_weights)
 # ----------------------------------------------------------------------------------------------
@@ -514,6 +550,48 @@ def test_voronoi_duplicate_sample_takes_the_floor():
     assert cnt[1] == 0 and cnt[0] > 0 and cnt[2] > 0 and cnt[0] + cnt[2] == 40 * 40
     s = cnt[0] + cnt[2] + 0.5
     assert abs(w[1] - 0.5 / s) < 1e-7 and abs(w.sum() - 1.0) < 1e-6
+
+
+def _f32_column_case(Ng=10, D=2.0 ** -7):
+    """Raster column a of the unit square whose binary64 abscissa X is not a binary32 number, and two
+    binary32 samples at binary32(X) -/+ D on one raster row: the far one (the side of binary32(X) away
+    from X) first, so that it wins every tie of a decision taken in binary32."""
+    base = _square_cell([0.0], [0.0])
+    fr = oracle.frame(4, base.verts[0], base.eta, base.mask)
+    x0, y0, step = fr["cx"] - fr["H"], fr["cy"] - fr["H"], fr["L"] / Ng
+    a = next(a for a in range(Ng) if float(np.float32(x0 + step * (a + 0.5))) != x0 + step * (a + 0.5))
+    X = x0 + step * (a + 0.5)
+    Xf = float(np.float32(X))
+    near, far = (Xf + D, Xf - D) if X > Xf else (Xf - D, Xf + D)
+    Yf = float(np.float32(y0 + step * 3.5))
+    assert float(np.float32(near)) == near and float(np.float32(far)) == far
+    return [far, near], [Yf, Yf], (x0, y0, step), a
+
+
+def test_voronoi_nearest_sample_is_decided_exactly():
+    """Eq. nn_assignment assigns each raster point to its nearest sample, an exact decision.  On the
+    column whose abscissa X binary32 cannot represent, two samples symmetric about binary32(X) are at
+    equal binary32 distances, while in exact arithmetic the sample on X's side is nearer for every
+    point of the column.  The counts must be those of exact rational arithmetic (ties to the lower
+    index), which differ from a decision taken in binary32."""
+    from fractions import Fraction as Fr
+    Ng = 10
+    xs, ys, (x0, y0, step), a = _f32_column_case(Ng)
+    _, cnt = oracle.voronoi_weights(_square_cell(xs, ys), Ng=Ng)
+    exact, f32 = [0, 0], [0, 0]
+    for b in range(Ng):
+        Y = y0 + step * (b + 0.5)
+        for a2 in range(Ng):
+            X = x0 + step * (a2 + 0.5)
+            d = [(Fr(X) - Fr(xs[i])) ** 2 + (Fr(Y) - Fr(ys[i])) ** 2 for i in range(2)]
+            exact[0 if d[0] <= d[1] else 1] += 1
+            Xf, Yf = np.float32(X), np.float32(Y)
+            e = [(Xf - np.float32(xs[i])) * (Xf - np.float32(xs[i])) + (Yf - np.float32(ys[i])) * (Yf - np.float32(ys[i]))
+                 for i in range(2)]
+            f32[0 if e[0] <= e[1] else 1] += 1
+    assert exact != f32                       # the case separates the two precisions
+    assert cnt.tolist() == exact
+    assert exact[1] == Ng * (Ng - a - 1) + Ng or exact[1] == Ng * (a + 1)   # the near sample owns column a
 
 
 def test_voronoi_weights_partition_the_window():
