@@ -1,8 +1,8 @@
 """FP64 CPU oracle for the ENUFFT type-1 transform, EMS and gradient (test infrastructure).
 
-Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use this
-package; the CUDA library never imports, links or calls it, and it shares no code with the
-library.  The arithmetic lives in ``enufft_oracle.c`` (plain C, FP64, direct sums, one function
+Only the tests, ``__graft_entry__.smoke()``, the CPU-baseline leg of ``bench.py`` and its untimed
+parity check use this package; the CUDA library never imports, links or calls it, and it shares no
+code with the library.  The arithmetic lives in ``enufft_oracle.c`` (plain C, FP64, direct sums, one function
 per passage of the paper); this module compiles it with gcc and marshals numpy arrays.
 """
 from __future__ import annotations
@@ -219,6 +219,62 @@ def ems(coeffs: np.ndarray, params: EMSParams = EMSParams(), mode_weights=None, 
                                params.sens_eps, _p(ks), _p(sel), _p(ret), _p(diag), int(nthreads))
     assert r == 0
     return ks, sel, ret, diag
+
+
+def pair_energies(coeffs: np.ndarray) -> dict:
+    """Sec. 2.2 pair energies E_p = |h_p|^2 + |h_-p|^2 of one P x P spectrum (binary64, no weights) over
+    the symmetric box |m|, |n| <= P/2 - 1 without DC, keyed by the pair index p = (n + P/2) P + (m + P/2)
+    of the half-plane member (n > 0, or n = 0 and m > 0)."""
+    c = np.asarray(coeffs, dtype=np.complex128)
+    P = c.shape[-1]
+    half = P // 2
+    out = {}
+    for n in range(0, half):
+        for m in range(-(half - 1), half):
+            if n == 0 and m <= 0:
+                continue
+            out[(n + half) * P + (m + half)] = abs(c[n + half, m + half]) ** 2 + abs(c[-n + half, -m + half]) ** 2
+    return out
+
+
+def mode_set_gate(got_coeffs, got_kstar, got_sel, ref_coeffs, params: EMSParams = EMSParams(), factor: float = 3.0):
+    """End-to-end EMS mode-set check of a mixed-precision spectrum against the binary64 one.
+
+    The selection of the binary64 oracle (ems on ref_coeffs) is compared with (got_kstar, got_sel)
+    cell by cell.  For a cell that differs, eta is the measured relative error of the pair energies
+    that decide the selection (the K_max + 1 largest oracle energies and both selections); the
+    mismatch is a near-tie only when a decision of the oracle is closer than `factor` * eta: a
+    relative gap between consecutive energies of the K_max + 1 largest (the order of the selection,
+    K* and the K_max boundary), the threshold margin of theta(K*), or an alpha_C that moves by at least
+    that margin when the energies carry a relative error `factor` * eta.  Returns a dict with
+    the number of cells, the mismatching cells with their margins, eta and verdict, and whether every
+    mismatch is a near-tie."""
+    got_coeffs = np.asarray(got_coeffs)
+    ref_coeffs = np.asarray(ref_coeffs)
+    got_kstar = np.asarray(got_kstar)
+    got_sel = np.asarray(got_sel)
+    oks, osel, _, _ = ems(ref_coeffs, params)
+    bad = np.nonzero((got_kstar != oks) | (got_sel != osel).any(1))[0]
+    out = []
+    for j in bad.tolist():
+        Eo = pair_energies(ref_coeffs[j])
+        Eg = pair_energies(got_coeffs[j])
+        keys = sorted(Eo, key=lambda p: (-Eo[p], p))[: params.k_max + 1]
+        keys += [int(p) for p in osel[j][: oks[j]]] + [int(p) for p in got_sel[j][: got_kstar[j]]]
+        eta = max(abs(Eg[p] - Eo[p]) / Eo[p] for p in keys if p in Eo and Eo[p] > 0)
+        prm = EMSParams(**{**params.__dict__, "sens_eps": factor * eta})
+        _, _, _, d = ems(ref_coeffs[j:j + 1], prm)
+        m_rank, m_theta, gap_kmax, sens = d[0, 6], d[0, 7], d[0, 10], d[0, 11]
+        top = sorted(Eo.values(), reverse=True)[: params.k_max + 1]
+        # smallest relative gap between consecutive energies of the head (the order of sel, K* and
+        # the K_max boundary all hang on these comparisons)
+        gap_order = min([(top[i] - top[i + 1]) / top[i] for i in range(len(top) - 1) if top[i] > 0] or [np.inf])
+        gaps = [abs(v) for v in (gap_order, m_theta) if np.isfinite(v)]
+        near = (min(gaps) if gaps else np.inf) <= factor * eta or (np.isfinite(sens) and sens >= abs(m_theta))
+        out.append(dict(cell=int(j), kstar_gpu=int(got_kstar[j]), kstar_oracle=int(oks[j]), margin_rank=float(m_rank),
+                        margin_theta=float(m_theta), gap_kmax=float(gap_kmax), gap_order=float(gap_order),
+                        alpha_sensitivity=float(sens), energy_err=float(eta), near_tie=bool(near)))
+    return dict(cells=int(len(oks)), mismatches=out, all_near_ties=all(m["near_tie"] for m in out))
 
 
 def ems_energies(E, params: EMSParams = EMSParams()):

@@ -175,24 +175,20 @@ def test_ems_mode_weights():
 
 
 def test_ems_end_to_end_against_fp64_oracle():
-    """Mode sets from the mixed GPU path equal the FP64 oracle's mode sets, except where the oracle's own
-    margins show a near-tie below the GPU coefficient error: a ranking gap (at K* or at the K_max
-    boundary) or a threshold margin within 100x that error, or an alpha_C that moves by more than the
-    threshold margin under an energy error of twice it.  Each mismatch is reported with its margins."""
-    wl = synth.make("tri20480_p64", seed=12, n_cells=48, q_scale=0.2)
+    """Mode sets from the mixed GPU path equal the FP64 oracle's mode sets (oracle.mode_set_gate).  A
+    cell whose selection differs passes only as a measured near-tie: some decision of the oracle (a gap
+    between consecutive head energies, the threshold margin, or the alpha_C shift) lies within three
+    times the relative energy error of that cell's deciding pairs, as measured against the oracle.
+    Every mismatch is reported with its margins."""
+    wl = synth.make("tri20480_p64", seed=12, n_cells=128, q_scale=0.2)
     g = _gpu(wl)
     plan = enufft.Plan.for_workload(g)
     c, ks, sel, ret = plan.type1_ems(g.x, g.y, g.h, g.w)
     ref = oracle.type1(wl)
-    err = _rel_l2(c.cpu().numpy(), ref).max()
-    oks, osel, oret, diag = oracle.ems(ref, OEMS(sens_eps=2 * err))
-    bad = np.nonzero((ks.cpu().numpy() != oks) | (sel.cpu().numpy() != osel).any(1))[0]
-    for j in bad:
-        m_rank, m_theta, gap_kmax, sens = diag[j, 6], diag[j, 7], diag[j, 10], diag[j, 11]
-        near_tie = np.nanmin(np.abs([m_rank, m_theta, gap_kmax])) < 100 * err or sens >= abs(m_theta)
-        assert near_tie, dict(cell=int(j), margin_rank=m_rank, margin_theta=m_theta, gap_kmax=gap_kmax,
-                              alpha_sensitivity=sens, coeff_err=err)
-    assert len(bad) <= 2
+    gate = oracle.mode_set_gate(c.cpu().numpy(), ks.cpu().numpy(), sel.cpu().numpy(), ref, OEMS())
+    assert gate["all_near_ties"], gate["mismatches"]
+    bad = [m["cell"] for m in gate["mismatches"]]
+    oks, osel, oret, _ = oracle.ems(ref, OEMS())
     good = np.setdiff1d(np.arange(len(oks)), bad)
     assert np.allclose(ret.cpu().numpy()[good], oret[good], rtol=1e-4)
 
@@ -334,24 +330,3 @@ def test_plain_fp32_path_matches_oracle(name, n, qs):
     assert err.max() <= 1e-5, err
     oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
     assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
-
-
-def test_full_size_sampled_parity_mixed2560():
-    """The full 2,560-cell n_f = 256 workload (1.06e9 samples) in the benchmark's launch configuration:
-    the largest cells (2e6 samples, spread in several parts), the smallest and a seeded random set,
-    checked on the central 32 x 32 modes against the oracle's sum for those modes."""
-    wl = synth.make("mixed2560_p128", seed=0, device="cuda")
-    plan = enufft.Plan.for_workload(wl)
-    c = plan.type1(wl.x, wl.y, wl.h, wl.w)
-    plan.sync_status()
-    counts = wl.counts().cpu()
-    order = torch.argsort(counts, descending=True)
-    rng = np.random.default_rng(1)
-    cells = sorted(set(order[:3].tolist() + order[-2:].tolist() + rng.choice(wl.n_cells, 3, replace=False).tolist()))
-    sub = wl.cell_slice(cells).to("cpu")
-    del wl
-    ref = oracle.type1(sub, P=32)
-    P, k = 128, 16
-    got = c[cells].cpu().numpy()[:, P // 2 - k:P // 2 + k, P // 2 - k:P // 2 + k]
-    err = _rel_l2(got, ref)
-    assert err.max() <= 1e-5, err
