@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "NU points/s, batched type-1 ENUFFT+EMS at rel-l2<=1e-5; mixed vs plain FP32, 1 B300"
-DEFAULT_WORKLOAD = "tri20480_p64"
+DEFAULT_WORKLOAD = "tri81920_p64_mixed"
 KERNEL_SOURCES = ["common.cuh", "fft.cuh", "ems.cuh", "forward.cuh", "inst_common.cuh", "inst_f32_128.cu"]
 
 
@@ -170,6 +170,59 @@ def _workload(args, seed, device):
     return wl
 
 
+def _rank_workload(args, ws, rank, device):
+    """This rank's share of the job.  The job is one seeded batch made of `ws` replicas of the named
+    workload (seeds 0 .. ws - 1, so the work per GPU stays that of one workload: weak scaling); its
+    cells are split over the ranks by shard.partition_cells (LPT on 16 Q + 8 P^2 bytes), and each rank
+    keeps its own cells of every replica.  At ws = 1 this is the workload itself."""
+    if ws == 1:
+        return _workload(args, seed=0, device=device)
+    from paper_2606_21278_b300.shard import partition_cells
+    reps = [_workload(args, seed=k, device=device) for k in range(ws)]
+    counts = np.concatenate([r.counts().cpu().numpy() for r in reps])
+    mine = partition_cells(counts, reps[0].modes, ws)[rank]
+    base = np.cumsum([0] + [r.n_cells for r in reps])
+    parts = []
+    for k, r in enumerate(reps):
+        sel = mine[(mine >= base[k]) & (mine < base[k + 1])] - base[k]
+        parts.append(r.cell_slice(torch.as_tensor(sel, device=r.offsets.device)))
+    cat = lambda f: torch.cat([getattr(q, f) for q in parts])
+    offs = [torch.zeros(1, dtype=torch.int64, device=parts[0].offsets.device)]
+    for q in parts:
+        offs.append(q.offsets[1:] + offs[-1][-1])
+    return synth.Workload(**{**parts[0].__dict__, "n_cells": int(sum(q.n_cells for q in parts)),
+                             "nverts": cat("nverts"), "verts": cat("verts"), "offsets": torch.cat(offs),
+                             "x": cat("x"), "y": cat("y"), "h": cat("h"), "w": cat("w")})
+
+
+def _capture(fn):
+    """CUDA graph of fn() (stream-ordered library calls only), warmed up on a side stream first."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def _time_graph(g, steps, warmup=2):
+    """Per-replay CUDA-event times (ms) of a captured graph on the current stream."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
 def run_reference(args):
     """The oracle (FP64 direct sums + EMS) on the host cores: every step is a bounded seeded sample
     of the workload's cells, sized from the warm-up so that the whole run takes about
@@ -217,70 +270,139 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _bf16_peak():
+    """Dense tensor-core peak (TFLOP/s) for a kernel timed on its own: the measured bf16 burst figure;
+    binary16 operands run at the same nominal rate (2.25 PFLOP/s dense for both)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get("bf16_tflops", 1800.0), "measured (bf16 burst; f16 at the same nominal rate)"
+    return 1800.0, "fallback"
+
+
+def _alg_bytes(wl, P, k_max):
+    """Algorithmic bytes of one type-1 + EMS pass: 16 B per sample in, 8 P^2 B of coefficients and
+    4 + 4 K_max + 8 B of EMS results per cell out."""
+    return 16 * wl.n_points + 8 * P * P * wl.n_cells + (4 + 4 * k_max + 8) * wl.n_cells
+
+
+def _route_timings(enufft, wl, args, prm, steps):
+    """Each execution route of the step on its own cells, in its own captured graph: the fused
+    spread/FFT kernel on the cells above the tensor-core threshold, the tensor-core direct sum on the
+    rest.  Returns a dict per route with its time and roofline (HBM bytes for the fused kernel; the
+    method's 8 P^2 Q flops per cell against the tensor peak for the direct sum)."""
+    P = wl.modes
+    cnt = wl.counts()
+    hbm, hbm_src = _peaks()
+    tc_peak, tc_src = _bf16_peak()
+    out = {}
+    tc = int(wl.tc_max_points)
+    groups = [("fused", torch.nonzero(cnt > tc).flatten() if tc > 0 else None, 0),
+              ("tensor_core", torch.nonzero(cnt <= tc).flatten() if tc > 0 else None, tc)]
+    for name, cells, thr in groups:
+        if cells is None or len(cells) == 0:
+            continue
+        sub = wl.cell_slice(cells)
+        plan = enufft.Plan.for_workload(sub, tc_max_points=(1 << 30) if thr else 0, kernel=args.kernel,
+                                        frame=args.frame)
+        co = plan.new_coeffs()
+        o = plan._ems_out(prm)
+        g = _capture(lambda: plan.type1_ems(sub.x, sub.y, sub.h, sub.w, prm, coeffs=co, out=o))
+        ms = float(np.mean(_time_graph(g, steps)))
+        plan.sync_status()
+        ab = _alg_bytes(sub, P, prm.k_max)
+        gbs = ab / (ms * 1e-3) / 1e9
+        r = {"cells": sub.n_cells, "points": sub.n_points, "ms": ms, "points_per_s": sub.n_points / (ms * 1e-3),
+             "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_source": hbm_src,
+                     "algorithmic_bytes_per_launch": ab}}
+        if name == "tensor_core":
+            fl = 8.0 * P * P * sub.n_points
+            tf = fl / (ms * 1e-3) / 1e12
+            r["tensor"] = {"achieved": tf, "peak": tc_peak, "unit": "TFLOP/s", "frac": tf / tc_peak,
+                           "peak_source": tc_src, "flops_per_launch": fl,
+                           "executed_tflops": 3 * tf, "note": "method's work 8 P^2 Q; the split f16 products execute 3x"}
+        out[name] = r
+        del g, plan, co, o, sub
+    return out
+
+
 def run_ours(args):
     import paper_2606_21278_b300 as enufft
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    wl = _workload(args, seed=rank, device="cuda")
+    wl = _rank_workload(args, ws, rank, "cuda")
     plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame)
     info = plan.info()
     prm = enufft.EMSParams()
     coeffs = plan.new_coeffs()
-    ks = torch.empty(wl.n_cells, dtype=torch.int32, device="cuda")
-    sel = torch.empty(wl.n_cells, prm.k_max, dtype=torch.int32, device="cuda")
-    ret = torch.empty(wl.n_cells, dtype=torch.float64, device="cuda")
-    import ctypes
-    lib = enufft.load_library()
-    pc = prm.c()
+    ks, sel, ret = plan._ems_out(prm)
     stream = torch.cuda.current_stream()
-    lib.enufft_set_stream(plan._h, ctypes.c_void_p(stream.cuda_stream))
-    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
 
     def step(x, y, h, w):
-        st = lib.enufft_type1_ems(plan._h, ptr(x), ptr(y), ptr(h), ptr(w), ptr(coeffs), None, 0, ctypes.byref(pc),
-                                  ptr(ks), ptr(sel), ptr(ret))
-        if st != 0:
-            raise RuntimeError(lib.enufft_last_error(plan._h).decode())
+        plan.type1_ems(x, y, h, w, prm, coeffs=coeffs, out=(ks, sel, ret))
 
+    # the step (every kernel of enufft_type1_ems) captured once in a CUDA graph and replayed
     for _ in range(args.warmup):
         step(wl.x, wl.y, wl.h, wl.w)
     torch.cuda.synchronize()
     plan.sync_status()
+    graph = _capture(lambda: step(wl.x, wl.y, wl.h, wl.w))
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     _barrier(ws)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        torch.cuda.nvtx.range_push("timed")
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
-            step(wl.x, wl.y, wl.h, wl.w)
+            graph.replay()
             ev[i][1].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
     _barrier(ws)
+    plan.sync_status()
     total_ms = _max_over_ranks(t0.elapsed_time(t1), ws)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     ms = total_ms / args.steps
     pts_all = _sum_over_ranks(float(wl.n_points), ws)
     value = pts_all / (ms * 1e-3)
-
-    # roofline of the dominant kernel (the fused type-1 + EMS kernel is the only kernel of the step)
     P = wl.modes
-    alg_bytes = 16 * wl.n_points + 8 * P * P * wl.n_cells + (4 + 4 * prm.k_max + 8) * wl.n_cells
-    kern_ms = float(np.mean(launch_ms))
     peak, peak_src = _peaks()
-    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+    tc_peak, _ = _bf16_peak()
+
+    # each route on its own (the dominant kernel's roofline is taken from its own launches)
+    routes = _route_timings(enufft, wl, args, prm, max(3, min(args.steps, 10))) if info["cells_large"] == 0 else {}
+    alg_all = _alg_bytes(wl, P, prm.k_max)
+    if info["cells_large"] == 0 and info["cells_tensor"] == 0:   # one route: the step itself
+        kms = float(np.mean(launch_ms))
+        gbs = alg_all / (kms * 1e-3) / 1e9
+        routes["fused"] = {"cells": wl.n_cells, "points": wl.n_points, "ms": kms, "points_per_s": wl.n_points / (kms * 1e-3),
+                           "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_all}}
+    if info["cells_large"]:
+        kern = "n_f = 256 route, whole step (sort, scale, tile spread, FFT, EMS finish)"
+        ach = alg_all / (float(np.mean(launch_ms)) * 1e-3) / 1e9
+    else:
+        fr = routes["fused"] if "fused" in routes else routes["tensor_core"]
+        kern = (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish"
+                + (", local-coordinate pre-pass)" if args.frame == "edge" else ")")) if "fused" in routes \
+            else "tc_nudft_kernel (+ EMS finish)"
+        ach = fr["hbm"]["achieved"]
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": _traffic(args.workload) if args.frame == "centroid" else None, "peak_source": peak_src,
-            "kernel": (f"type1_fused_kernel<float,{info['fine_grid']},{info['kernel_width']}> (+ EMS finish"
-                       + (", local-coordinate pre-pass)" if args.frame == "edge" else ")") if info["cells_fused"]
-                                  else "n_f = 256 route, whole step (sort, scale, tile spread, FFT, EMS finish)"),
-            "algorithmic_bytes_per_launch": alg_bytes}
+            "kernel": kern, "algorithmic_bytes_per_launch": routes["fused"]["hbm"]["algorithmic_bytes_per_launch"]
+            if "fused" in routes else alg_all}
+    # the whole step against the batch roofline max(bytes / HBM, method flops / tensor peak)
+    tc_flops = 8.0 * P * P * sum(int(c) for c in wl.counts()[wl.counts() <= wl.tc_max_points].tolist()) \
+        if wl.tc_max_points > 0 else 0.0
+    t_roof = max(alg_all / (peak * 1e9), tc_flops / (tc_peak * 1e12))
+    step_roof = {"t_roof_ms": 1e3 * t_roof, "t_step_ms": ms, "frac": 1e3 * t_roof / ms,
+                 "bound": "hbm" if alg_all / (peak * 1e9) >= tc_flops / (tc_peak * 1e12) else "tensor",
+                 "algorithmic_bytes": alg_all, "tensor_flops": tc_flops}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     hx, hy, hh, hw = (t.cpu().pin_memory() for t in (wl.x, wl.y, wl.h, wl.w))
@@ -310,23 +432,47 @@ def run_ours(args):
     e2e_ms = _max_over_ranks(a.elapsed_time(b), ws) / e2e_steps
     h2d = 4 * wl.x.element_size() * wl.n_points
     d2h = ks.numel() * 4 + sel.numel() * 4 + ret.numel() * 8
+    del hx, hy, hh, hw, dx, dy, dh, dw
 
-    # sampled parity of the benchmarked run against the oracle (a few cells; CPU, untimed)
+    # untimed parity of the benchmarked spectra against the binary64 oracle on a seeded sample of
+    # cells (the 16 largest, the largest and smallest of the tensor-core cells, the rest random):
+    # coefficient rel-l2, the end-to-end EMS mode-set gate, and the EMS taken in the kernel's precision
     parity = None
     if rank == 0 and not args.no_check:
         import oracle
-        step(wl.x, wl.y, wl.h, wl.w)
+        graph.replay()
         torch.cuda.synchronize()
         cnt = wl.counts().cpu()
-        cells = sorted(set(torch.argsort(cnt, descending=True)[:2].tolist() + [0, wl.n_cells // 2, wl.n_cells - 1]))
+        order = torch.argsort(cnt, descending=True).tolist()
+        pick = set(order[:16])
+        if wl.tc_max_points > 0:
+            tcc = [c for c in order if cnt[c] <= wl.tc_max_points]
+            pick.update(tcc[:8] + tcc[-4:])
+        rng = np.random.default_rng(1)
+        target = min(wl.n_cells, args.check_cells)
+        for c in rng.permutation(wl.n_cells).tolist():
+            if len(pick) >= target:
+                break
+            pick.add(c)
+        cells = sorted(pick)
         sub = wl.cell_slice(cells).to("cpu")
+        t_o = time.perf_counter()
         ref = oracle.type1(sub)
+        t_o = time.perf_counter() - t_o
         got = coeffs[cells].cpu().numpy()
         rel = np.linalg.norm((got - ref).reshape(len(cells), -1), axis=1) / np.linalg.norm(ref.reshape(len(cells), -1), axis=1)
+        gks, gsel = ks[cells].cpu().numpy(), sel[cells].cpu().numpy()
+        gate = oracle.mode_set_gate(got, gks, gsel, ref, oracle.EMSParams())
         oks, osel, _, _ = oracle.ems(got, oracle.EMSParams(), energy_fp32=True)
-        parity = {"cells": len(cells), "max_rel_l2": float(rel.max()),
-                  "ems_identical": bool(np.array_equal(oks, ks[cells].cpu().numpy()) and
-                                        np.array_equal(osel, sel[cells].cpu().numpy()))}
+        tc_in = int(sum(1 for c in cells if wl.tc_max_points and cnt[c] <= wl.tc_max_points))
+        parity = {"cells": len(cells), "tensor_core_cells": tc_in, "points": sub.n_points,
+                  "max_rel_l2": float(rel.max()), "median_rel_l2": float(np.median(rel)),
+                  "ems_fp64_mismatches": len(gate["mismatches"]),
+                  "ems_fp64_near_ties": sum(1 for m in gate["mismatches"] if m["near_tie"]),
+                  "ems_identical": len(gate["mismatches"]) == 0,
+                  "mismatches": gate["mismatches"][:8],
+                  "ems_kernel_precision_identical": bool(np.array_equal(oks, gks) and np.array_equal(osel, gsel)),
+                  "oracle_s": t_o}
 
     # Sec. 3.2 diagnostics on the benchmarked spectra and selection (reconstruction at every sample,
     # relative RMSE, Parseval variances), timed like the step; fused-route plans only
@@ -334,25 +480,20 @@ def run_ours(args):
     if not args.no_reconstruct and info["cells_large"] == 0:
         hrec = torch.empty_like(wl.h)
         stats = torch.empty(wl.n_cells, 4, dtype=torch.float64, device="cuda")
+        lib = enufft.load_library()
+        import ctypes
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
 
         def rstep():
+            lib.enufft_set_stream(plan._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
             st = lib.enufft_reconstruct(plan._h, ptr(coeffs), ptr(ks), ptr(sel), prm.k_max, ptr(wl.x), ptr(wl.y),
                                         ptr(wl.h), ptr(wl.w), ptr(hrec), ptr(stats))
             if st != 0:
                 raise RuntimeError(lib.enufft_last_error(plan._h).decode())
 
-        for _ in range(3):
-            rstep()
-        torch.cuda.synchronize()
-        _barrier(ws)
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rg = _capture(rstep)
         rsteps = max(3, min(args.steps, 20))
-        r0.record(stream)
-        for _ in range(rsteps):
-            rstep()
-        r1.record(stream)
-        torch.cuda.synchronize()
-        rms = _max_over_ranks(r0.elapsed_time(r1), ws) / rsteps
+        rms = _max_over_ranks(float(np.mean(_time_graph(rg, rsteps))), ws)
         plan.sync_status()
         rbytes = 20 * wl.n_points + (8 * P * P + 4 + 4 * prm.k_max + 32) * wl.n_cells
         rach = rbytes / (rms * 1e-3) / 1e9
@@ -361,28 +502,21 @@ def run_ours(args):
                  "roofline": {"bound": "hbm", "achieved": rach, "peak": peak, "unit": "GB/s", "frac": rach / peak,
                               "algorithmic_bytes_per_launch": rbytes},
                  "median_eps_rel": float(stats[:, 0].median().item())}
+        del rg, hrec, stats
 
     # Voronoi quadrature weights by raster sampling (App. A) for the workload's samples, ng = 64:
-    # nearest windowed sample of every raster point (bucketed search); binary32 plans of the fused
-    # route only (cells of more than 16384 samples fall back to a brute-force search)
+    # a once-per-mesh preprocessing step, timed for reference (binary32 plans of the fused route)
     voronoi = None
-    if not args.no_voronoi and info["cells_large"] == 0 and wl.x.dtype == torch.float32:
+    if not args.no_voronoi and info["cells_large"] == 0 and wl.x.dtype == torch.float32 and args.frame == "centroid":
         ng = 64
         wv = torch.empty_like(wl.w)
-
-        def vstep():
-            st = lib.enufft_voronoi_weights(plan._h, ptr(wl.x), ptr(wl.y), ng, ptr(wv))
-            if st != 0:
-                raise RuntimeError(lib.enufft_last_error(plan._h).decode())
-
-        vstep()
+        plan.voronoi_weights(wl.x, wl.y, ng)
         torch.cuda.synchronize()
-        _barrier(ws)
         v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         vsteps = 3
         v0.record(stream)
         for _ in range(vsteps):
-            vstep()
+            wv = plan.voronoi_weights(wl.x, wl.y, ng)
         v1.record(stream)
         torch.cuda.synchronize()
         vms = _max_over_ranks(v0.elapsed_time(v1), ws) / vsteps
@@ -390,7 +524,46 @@ def run_ours(args):
         searches = float(ng * ng) * wl.n_cells
         voronoi = {"ms": vms, "value": pts_all / (vms * 1e-3), "unit": "points/s", "steps": vsteps, "ng": ng,
                    "raster_searches_per_s": _sum_over_ranks(searches, ws) / (vms * 1e-3),
-                   "kernel": "voronoi_kernel (bucketed nearest sample, binary32)"}
+                   "kernel": "voronoi_kernel (bucketed nearest sample, certified binary32, binary64 near ties)"}
+        del wv
+
+    # the differentiation workload (4,096 hexagons, 48 x 48 modes): forward type-1 + EMS, loss L =
+    # sum of the EMS-retained power over cells (one binary64 scalar all-reduced over the ranks, the
+    # only collective), backward through the hand-written adjoint to dL/dh and dL/dw
+    gradient = None
+    if not args.no_gradient:
+        gw_ = synth.make("hex4096_p48", seed=rank, device="cuda")
+        gplan = enufft.Plan.for_workload(gw_)
+        hh_ = gw_.h.clone().requires_grad_(True)
+        ww_ = gw_.w.clone().requires_grad_(True)
+
+        def gstep():
+            hh_.grad = None
+            ww_.grad = None
+            power, _, _, _ = enufft.EMSRetainedPower.apply(hh_, ww_, gplan, gw_.x, gw_.y)
+            L = power.sum()
+            L.backward()
+            return L
+
+        for _ in range(3):
+            gstep()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gsteps = max(3, min(args.steps, 10))
+        g0.record(stream)
+        for _ in range(gsteps):
+            L = gstep()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = _max_over_ranks(g0.elapsed_time(g1), ws) / gsteps
+        gplan.sync_status()
+        L_all = _sum_over_ranks(float(L.item()), ws)
+        gpts = _sum_over_ranks(float(gw_.n_points), ws)
+        gradient = {"workload": "hex4096_p48", "ms": gms, "value": gpts / (gms * 1e-3), "unit": "points/s",
+                    "steps": gsteps, "loss": L_all,
+                    "kernels": "type1_fused_kernel + ems_finish_kernel + ems_backward_kernel + type1_adjoint_kernel",
+                    "collective": "one binary64 scalar all-reduce of L per step" if ws > 1 else "none (1 rank)"}
+        del gplan, hh_, ww_, gw_
 
     # the plain binary32 per-cell path on the same workload (one launch sequence per cell), for the
     # speed-up the metric states; timed the same way, fewer steps
@@ -399,13 +572,10 @@ def run_ours(args):
         pplan = enufft.Plan.for_workload(wl, precision="fp32", tc_max_points=0, kernel=args.kernel,
                                          frame=args.frame)
         pco = pplan.new_coeffs()
-        lib.enufft_set_stream(pplan._h, ctypes.c_void_p(stream.cuda_stream))
+        pout = pplan._ems_out(prm)
 
         def pstep():
-            st = lib.enufft_type1_ems(pplan._h, ptr(wl.x), ptr(wl.y), ptr(wl.h), ptr(wl.w), ptr(pco), None, 0,
-                                      ctypes.byref(pc), ptr(ks), ptr(sel), ptr(ret))
-            if st != 0:
-                raise RuntimeError(lib.enufft_last_error(pplan._h).decode())
+            pplan.type1_ems(wl.x, wl.y, wl.h, wl.w, prm, coeffs=pco, out=pout)
 
         psteps = 3
         pstep()
@@ -420,9 +590,9 @@ def run_ours(args):
         pms = _max_over_ranks(a0.elapsed_time(a1), ws) / psteps
         pplan.sync_status()
         plain = {"value": pts_all / (pms * 1e-3), "unit": "points/s", "ms_per_step": pms, "steps": psteps,
-                 "speedup": (pts_all / (ms * 1e-3)) / (pts_all / (pms * 1e-3)),
-                 "launches_per_step": pplan.info()["kernels_per_type1_ems"]}
-        del pplan, pco
+                 "speedup": pms / ms, "launches_per_step": pplan.info()["kernels_per_type1_ems"],
+                 "note": "one launch sequence per cell (memset, spread, row FFT, column FFT, deconvolve) + EMS"}
+        del pplan, pco, pout
 
     cpu_base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -438,19 +608,25 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "n_cells": wl.n_cells, "n_points": wl.n_points, "modes": P,
-                           "cells_tensor_core": info["cells_tensor"], "tc_max_points": wl.tc_max_points,
+                           "cells_fused": info["cells_fused"], "cells_tensor_core": info["cells_tensor"],
+                           "cells_large": info["cells_large"], "tc_max_points": wl.tc_max_points,
                            **({"q_scale": args.q_scale} if args.q_scale != 1.0 else {}),
                            **({"max_q": args.max_q} if args.max_q is not None else {}),
+                           **({"cells_subset": args.cells} if args.cells is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
-                           "kernel": args.kernel, "frame": args.frame, "precision": "mixed", "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
+                           "kernel": args.kernel, "frame": args.frame, "precision": "mixed",
+                           "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
+                           "timing": "one CUDA-graph replay of enufft_type1_ems per step",
                            "l2": f"inputs larger than L2 ({16 * wl.n_points / 1e9:.2f} GB of samples per step)",
-                           "parallelism": f"cells sharded, {ws} rank(s)"},
-                "roofline": roof, "cpu_baseline": cpu_base,
+                           "parallelism": (f"cells of {ws} seeded replicas split over {ws} ranks by LPT"
+                                           if ws > 1 else "1 rank")},
+                "roofline": roof, "routes": routes, "step_roofline": step_roof, "cpu_baseline": cpu_base,
                 "e2e": {"value": pts_all / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "plain_fp32": plain,
                 "reconstruct": recon,
                 "voronoi": voronoi,
+                "gradient": gradient,
                 "gpu_launches": info["kernels_per_type1_ems"] * args.steps,
                 "clocks": clk.summary(), "parity": parity}
         print(json.dumps(line), flush=True)
@@ -504,6 +680,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 per-cell path")
     ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
+    ap.add_argument("--no-gradient", action="store_true", help="skip timing the differentiation workload")
+    ap.add_argument("--check-cells", type=int, default=1024,
+                    help="cells of the untimed parity check against the binary64 oracle")
     ap.add_argument("--kernel", default="es", choices=["es", "kb"],
                     help="spreading kernel: exponential of semicircle (default) or Kaiser-Bessel")
     ap.add_argument("--frame", default="centroid", choices=["centroid", "edge"],

@@ -87,9 +87,10 @@ class Workload:
         cnt = hi - lo
         new_off = torch.zeros(len(cells) + 1, dtype=torch.int64, device=cnt.device)
         new_off[1:] = torch.cumsum(cnt, 0)
-        idx = torch.cat([torch.arange(int(a), int(b), device=cnt.device)
-                         for a, b in zip(lo.tolist(), hi.tolist())]) if len(cells) else \
-            torch.zeros(0, dtype=torch.int64, device=cnt.device)
+        total = int(new_off[-1])
+        # sample j of the slice: its cell's first source sample + its rank inside the cell
+        idx = (torch.repeat_interleave(lo - new_off[:-1], cnt, output_size=total)
+               + torch.arange(total, dtype=torch.int64, device=cnt.device))
         kw = dict(self.__dict__)
         kw.update(n_cells=len(cells), nverts=self.nverts[cells], verts=self.verts[cells],
                   offsets=new_off, x=self.x[idx], y=self.y[idx], h=self.h[idx], w=self.w[idx])

@@ -49,6 +49,50 @@ def _rank_main(rank, world, port, counts, out):
         dist.destroy_process_group()
 
 
+def _cell_keys(wl):
+    """(sample count, first sample's x, y) of every cell: identifies a cell of the seeded replicas."""
+    off = wl.offsets.tolist()
+    return sorted((off[j + 1] - off[j], float(wl.x[off[j]]), float(wl.y[off[j]])) for j in range(wl.n_cells)
+                  if off[j + 1] > off[j])
+
+
+def _slice_main(rank, world, port, out):
+    import argparse
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b = _bench_module()
+        args = argparse.Namespace(workload="tri20480_p64", cells=40, q_scale=0.02, max_q=None, tc_max_points=None,
+                                  frame="centroid")
+        wl = b._rank_workload(args, world, rank, "cpu")
+        keys = [None] * world
+        dist.all_gather_object(keys, (wl.n_cells, wl.n_points, _cell_keys(wl)))
+        out[rank] = keys
+        # the gradient path's only collective: one binary64 scalar summed over the ranks
+        out[f"L{rank}"] = b._sum_over_ranks(float(rank + 0.5), world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_one_seeded_batch():
+    """bench.py's job is one seeded batch of `world` replicas split by LPT: the union of the two ranks'
+    cells is exactly the set of cells of the replicas, no cell twice, and the loss reduction adds the
+    ranks' scalars."""
+    import synth
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_slice_main, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
+    per_rank = out[0]
+    assert per_rank == out[1]
+    union = sorted(k for r in range(world) for k in per_rank[r][2])
+    expect = sorted(k for s in range(world)
+                    for k in _cell_keys(synth.make("tri20480_p64", seed=s, n_cells=40, q_scale=0.02)))
+    assert union == expect
+    assert sum(per_rank[r][0] for r in range(world)) == 2 * 40
+    assert out["L0"] == out["L1"] == 2.0
+
+
 def test_two_gloo_ranks_reduce_and_agree_on_the_partition():
     world = 2
     counts = np.random.default_rng(0).integers(500, 20000, size=301)
