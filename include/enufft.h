@@ -250,7 +250,9 @@ enufft_status enufft_set_stream(enufft_plan plan, void *cuda_stream);
  *     (different streams, or different host threads) race on it and must be serialised by the
  *     caller.  Nothing in it needs to start at zero.
  *   - The first call on each device looks up the array's device address (with that device
- *     current); make that first call before any stream capture.
+ *     current); make that first call before any stream capture.  The address is kept for the
+ *     life of the process: after cudaDeviceReset (or any other teardown of the device's primary
+ *     context) it is stale, so do not call this entry point again in that process.
  */
 enufft_status enufft_ems_noalloc(int modes, int64_t n_cells, const void *d_coeffs,
                                  const double *d_mode_weights, int mode_weights_per_cell,
@@ -267,7 +269,10 @@ enufft_status enufft_ems_noalloc(int modes, int64_t n_cells, const void *d_coeff
  */
 enufft_status enufft_selftest_wait_timeout(enufft_plan plan, unsigned polls);
 
-/* Synchronise the plan's stream and report (then clear) any latched device-side condition. */
+/* Synchronise the plan's stream and report (then clear) any latched device-side condition:
+ * non-finite samples (skipped), degenerate cell polygons (cells skipped), an edge-frame sample
+ * placed at its cell centroid (ENUFFT_ERR_DEVICE for these; the message names each), or an
+ * exhausted bounded wait (ENUFFT_ERR_TIMEOUT). */
 enufft_status enufft_sync_status(enufft_plan plan);
 
 /* Human-readable text of the last error on this plan (plan == NULL: of the calling thread). */

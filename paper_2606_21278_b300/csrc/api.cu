@@ -665,6 +665,7 @@ enufft_status enufft_sync_status(enufft_plan p) {
         if (st & ST_NONFINITE) m += " non-finite sample(s) skipped;";
         if (st & ST_BADCELL) m += " degenerate cell polygon(s);";
         if (st & ST_TIMEOUT) m += " bounded wait expired;";
+        if (st & ST_MOVED) m += " edge frame: sample(s) placed at the cell centroid (no binary32 point inside the window);";
         return fail(p, (st & ST_TIMEOUT) ? ENUFFT_ERR_TIMEOUT : ENUFFT_ERR_DEVICE, m);
     }
     return ENUFFT_OK;
@@ -872,7 +873,7 @@ static enufft_status edge_prepass(enufft_plan p, const void*& x, const void*& y)
     // one wave of persistent blocks: three resident per SM (the kernel's launch bound)
     const int grid = (int)std::min<int64_t>(p->n_cells, (int64_t)p->num_sms * 3);
     cudaError_t e = launch_edge_frame(p->dbl, x, y, p->d_offsets, p->d_cells, p->d_rot, p->n_cells, p->d_vx, p->d_vy,
-                                      grid, p->stream);
+                                      p->d_ctr + 2, grid, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "edge frame: launch");
     x = p->d_vx;
     y = p->d_vy;

@@ -37,6 +37,8 @@ enum : unsigned {
     ST_NONFINITE = 1u,   // a sample had a non-finite coordinate, elevation or weight (skipped)
     ST_TIMEOUT = 2u,     // a bounded wait gave up
     ST_BADCELL = 4u,     // a cell polygon was degenerate (zero area or bad vertex count)
+    ST_MOVED = 8u,       // edge frame: a windowed sample had no binary32 local point inside the window
+                         // near its own and was placed at the cell centroid
 };
 
 // --------------------------------------------------------------------------------------------

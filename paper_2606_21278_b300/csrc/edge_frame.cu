@@ -15,8 +15,9 @@
 //     window test rejects.  A sample within the margin is decided by the definition's binary64
 //     computation; if inside, v rounded to binary32 is stored, moved toward the centroid by the
 //     smallest of a few growing factors (1 - 2^-23, 1 - 2^-21, ...) that keeps the binary64 test
-//     true, the centroid itself as the last resort (it is inside every convex cell, B and the disk).
-//     Later window tests therefore agree with the exact decision.
+//     true, the centroid itself as the last resort (it is inside every convex cell, B and the disk;
+//     that case latches ST_MOVED, reported by enufft_sync_status).  Later window tests therefore
+//     agree with the exact decision.
 //   - Non-finite coordinates are copied through, so the routes report them as before.
 #include "internal.h"
 
@@ -55,7 +56,8 @@ __device__ __forceinline__ void ef_dot2(float ah, float al, float bh, float bl, 
 }
 
 // the definition's binary64 decision for a sample within the binary32 margin, and its stored point
-__device__ __noinline__ float2 edge_exact_f32(const CellConst& cc, const FrameRot& fr, double px, double py, float far) {
+__device__ __noinline__ float2 edge_exact_f32(const CellConst& cc, const FrameRot& fr, double px, double py, float far,
+                                              unsigned* status) {
     const double dx = __dsub_rn(px, fr.cx), dy = __dsub_rn(py, fr.cy);
     const double ux = __dadd_rn(__dmul_rn(fr.c, dx), __dmul_rn(fr.s, dy));
     const double uy = __dadd_rn(__dmul_rn(-fr.s, dx), __dmul_rn(fr.c, dy));
@@ -68,14 +70,16 @@ __device__ __noinline__ float2 edge_exact_f32(const CellConst& cc, const FrameRo
         fy = __double2float_rn(__dmul_rn(uy, sh));
         in = window_f64(cc, (double)fx, (double)fy);
     }
-    return in ? make_float2(fx, fy) : make_float2(0.0f, 0.0f);
+    if (in) return make_float2(fx, fy);
+    atomicOr(status, ST_MOVED);   // reported: the stored point is no longer the sample's own
+    return make_float2(0.0f, 0.0f);
 }
 
 // the local coordinates of one sample (see the file comment)
 template <typename T>
 __device__ __forceinline__ void edge_local(const CellConst& cc, const FastFrame& ff, const FrameRot& fr, float cxh,
                                            float cxl, float cyh, float cyl, float ch, float cl, float sh, float sl,
-                                           float far, T px, T py, T& ox, T& oy) {
+                                           float far, T px, T py, T& ox, T& oy, unsigned* status) {
     if (!(isfinite(px) && isfinite(py))) {   // copied through: the routes report them
         ox = px;
         oy = py;
@@ -106,7 +110,7 @@ __device__ __forceinline__ void edge_local(const CellConst& cc, const FastFrame&
         else if (win == 0)
             v = make_float2(far, far);
         else
-            v = edge_exact_f32(cc, fr, (double)px, (double)py, far);
+            v = edge_exact_f32(cc, fr, (double)px, (double)py, far, status);
         ox = v.x;
         oy = v.y;
     }
@@ -119,7 +123,7 @@ template <typename T>
 static __global__ void __launch_bounds__(kEdgeThreads, 3)
 edge_frame_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __restrict__ offsets,
                   const CellConst* __restrict__ cells, const FrameRot* __restrict__ rot, int64_t n_cells,
-                  T* __restrict__ vx, T* __restrict__ vy) {
+                  T* __restrict__ vx, T* __restrict__ vy, unsigned* status) {
     __shared__ __align__(16) CellConst scc;
     __shared__ FrameRot sfr;
     static_assert(sizeof(CellConst) % 16 == 0, "cell constants copied in 16-byte words");
@@ -156,7 +160,7 @@ edge_frame_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_
                 const int64_t q = qb + (int64_t)k * blockDim.x;
                 if (q < q1) {
                     T ox, oy;
-                    edge_local<T>(cc, ff, fr, cxh, cxl, cyh, cyl, ch, cl, sh, sl, far, px[k], py[k], ox, oy);
+                    edge_local<T>(cc, ff, fr, cxh, cxl, cyh, cyl, ch, cl, sh, sl, far, px[k], py[k], ox, oy, status);
                     vx[q] = ox;
                     vy[q] = oy;
                 }
@@ -166,14 +170,15 @@ edge_frame_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_
 }
 
 cudaError_t launch_edge_frame(bool dbl, const void* x, const void* y, const int64_t* offsets, const CellConst* cells,
-                              const FrameRot* rot, int64_t n_cells, void* vx, void* vy, int grid, cudaStream_t s) {
+                              const FrameRot* rot, int64_t n_cells, void* vx, void* vy, unsigned* status, int grid,
+                              cudaStream_t s) {
     if (n_cells <= 0) return cudaSuccess;
     if (dbl)
         edge_frame_kernel<double><<<grid, kEdgeThreads, 0, s>>>((const double*)x, (const double*)y, offsets, cells, rot,
-                                                                n_cells, (double*)vx, (double*)vy);
+                                                                n_cells, (double*)vx, (double*)vy, status);
     else
         edge_frame_kernel<float><<<grid, kEdgeThreads, 0, s>>>((const float*)x, (const float*)y, offsets, cells, rot,
-                                                               n_cells, (float*)vx, (float*)vy);
+                                                               n_cells, (float*)vx, (float*)vy, status);
     return cudaGetLastError();
 }
 

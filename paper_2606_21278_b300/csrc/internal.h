@@ -19,7 +19,8 @@ struct FrameRot {
 // Per-call pre-pass of edge-frame plans (edge_frame.cu): the local coordinates v = R (x - x-bar) of
 // every sample into (vx, vy), see enufft_frame.
 cudaError_t launch_edge_frame(bool dbl, const void* x, const void* y, const int64_t* offsets, const CellConst* cells,
-                              const FrameRot* rot, int64_t n_cells, void* vx, void* vy, int grid, cudaStream_t s);
+                              const FrameRot* rot, int64_t n_cells, void* vx, void* vy, unsigned* status, int grid,
+                              cudaStream_t s);
 
 // Is (precision, n_f, W) compiled?  Shared-memory bytes and threads of the fused kernels.
 bool fused_supported(bool dbl, int nf, int w);
