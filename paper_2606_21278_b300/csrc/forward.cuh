@@ -30,6 +30,7 @@
 namespace enufft {
 
 constexpr int kMaxHalf = 64;   // P/2 <= 64
+constexpr int kSpreadPerThread = 4;   // samples per thread and chunk of the binary32 spreading
 
 #ifndef ENUFFT_FWD_MINB
 #define ENUFFT_FWD_MINB 2   // co-resident 512-thread blocks per SM of the binary32 fused kernels
@@ -75,9 +76,15 @@ struct FwdCfg {
     static constexpr size_t grid_bytes = sizeof(T) * (size_t)GR * GS;
     static constexpr size_t c1_bytes_min = sizeof(cplx<T>) * (size_t)NF * C1S_MAX;
     static constexpr size_t ems_bytes = ems_smem_bytes(NWARPS, kEmsMaxK);
-    static constexpr size_t c1_bytes = c1_bytes_min > ems_bytes ? c1_bytes_min : ems_bytes;
+    // binary32 spreading takes the samples in chunks of CHUNK, each staged as 16-byte records in the
+    // half-spectrum area (free until the row transforms)
+    static constexpr int CHUNK = NT * kSpreadPerThread;
+    static constexpr size_t rec_bytes = sizeof(T) == 4 ? (size_t)CHUNK * 16 : 0;
+    static constexpr size_t c1a_bytes = c1_bytes_min > ems_bytes ? c1_bytes_min : ems_bytes;
+    static constexpr size_t c1_bytes = c1a_bytes > rec_bytes ? c1a_bytes : rec_bytes;
     static constexpr size_t tw_bytes = sizeof(cplx<T>) * NF;
-    static constexpr size_t tail_bytes = sizeof(CellConst) + 16 + sizeof(T) * (kMaxHalf + 1) + 4 * NWARPS + 16;
+    static constexpr size_t tail_bytes =
+        sizeof(CellConst) + 16 + sizeof(T) * (kMaxHalf + 1) + 8 * NWARPS + 16 + 2 * 32 * sizeof(int);
     static constexpr size_t smem_bytes = grid_bytes + c1_bytes + tw_bytes + tail_bytes;
     // after the row pass the grid memory holds the staged P x P spectrum followed by the column
     // teams' workspaces
@@ -152,9 +159,9 @@ __device__ __forceinline__ void kernel_pieces(const KernelPoly& kp, float u, flo
 // node r0 of each dimension and the W kernel values there.  Returns false for samples outside
 // the window (or non-finite ones, which also latch ST_NONFINITE).
 template <int NF, int W>
-__device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __restrict__ edge, const CellConst& cc,
-                                         const KernelPoly& kp, float px, float py, int& r0x, int& r0y,
-                                         float (&kx)[W], float (&ky)[W], unsigned* status) {
+__device__ __forceinline__ bool prep_coords_f32(const FastFrame& ff, const float4* __restrict__ edge,
+                                                const CellConst& cc, float px, float py, int& r0x, int& r0y,
+                                                float& argx, float& argy, unsigned* status) {
     if (!(isfinite(px) && isfinite(py))) {
         atomicOr(status, ST_NONFINITE);
         return false;
@@ -175,8 +182,19 @@ __device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __re
     const float corrx = __fmaf_rn(uxh, ff.scl, uxl * ff.sch), corry = __fmaf_rn(uyh, ff.scl, uyl * ff.sch);
     const float tx = __fmaf_rn(-uxh, ff.sch, (float)(r0x - NF / 2) + 0.5f * W) - corrx;
     const float ty = __fmaf_rn(-uyh, ff.sch, (float)(r0y - NF / 2) + 0.5f * W) - corry;
-    kernel_pieces<W>(kp, __fmaf_rn(2.0f, tx, -1.0f), kx);
-    kernel_pieces<W>(kp, __fmaf_rn(2.0f, ty, -1.0f), ky);
+    argx = __fmaf_rn(2.0f, tx, -1.0f);
+    argy = __fmaf_rn(2.0f, ty, -1.0f);
+    return true;
+}
+
+template <int NF, int W>
+__device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __restrict__ edge, const CellConst& cc,
+                                         const KernelPoly& kp, float px, float py, int& r0x, int& r0y,
+                                         float (&kx)[W], float (&ky)[W], unsigned* status) {
+    float ax, ay;
+    if (!prep_coords_f32<NF, W>(ff, edge, cc, px, py, r0x, r0y, ax, ay, status)) return false;
+    kernel_pieces<W>(kp, ax, kx);
+    kernel_pieces<W>(kp, ay, ky);
     return true;
 }
 
@@ -218,6 +236,133 @@ __device__ __forceinline__ void spread_taps(unsigned addr, const float (&kx)[W],
             spread_taps<W, GS, J, I + 1>(addr, kx, ky, c);
         } else {
             spread_taps<W, GS, J + 1, 0>(addr, kx, ky, c);
+        }
+    }
+}
+
+// The W kernel pieces at u from the first (W + 1) / 2 fits: the kernel is even, so piece W - 1 - i at
+// u equals piece i at -u.  With p_i(u) = E_i(u^2) + u O_i(u^2) both come from one evaluation of the
+// even and odd parts (Horner in u^2).
+template <int W>
+__device__ __forceinline__ void kernel_pieces_sym(const KernelPoly& kp, float u, float (&v)[W]) {
+    constexpr int DEG = poly_deg(W), NE = (DEG + 1) / 2, NO = DEG / 2;
+    const float u2 = u * u;
+#pragma unroll
+    for (int i = 0; i < (W + 1) / 2; ++i) {
+        float e = kp.c[i][2 * (NE - 1)];
+#pragma unroll
+        for (int k = NE - 2; k >= 0; --k) e = __fmaf_rn(e, u2, kp.c[i][2 * k]);
+        float o = kp.c[i][2 * (NO - 1) + 1];
+#pragma unroll
+        for (int k = NO - 2; k >= 0; --k) o = __fmaf_rn(o, u2, kp.c[i][2 * k + 1]);
+        v[i] = __fmaf_rn(u, o, e);
+        if (W - 1 - i != i) v[W - 1 - i] = __fmaf_rn(-u, o, e);
+    }
+}
+
+// Rounding to the nearest integer by one multiply-add: for |v| < 2^22, v + 1.5 * 2^23 lies in
+// [2^23, 2^24), where binary32 numbers are the integers, so the sum rounds v to the nearest integer
+// and its bit pattern is that integer plus the pattern of 1.5 * 2^23.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;
+
+// the W x W taps of one sample: cs (c times the cell's fixed-point scale, |cs| <= 2^21) times the
+// separable kernel, rounded to integers (products below 2^22 in magnitude)
+template <int W, int GS, int J = 0, int I = 0>
+__device__ __forceinline__ void spread_taps_rn(unsigned addr, const float (&kx)[W], const float (&ky)[W], float cj,
+                                               float cs) {
+    if constexpr (J < W) {
+        if constexpr (I == 0) cj = cs * ky[J];
+        if constexpr (I < W) {
+            red_smem<J * GS + I>(addr, __float_as_int(__fmaf_rn(cj, kx[I], kRoundMagic)) - kRoundMagicBits);
+            spread_taps_rn<W, GS, J, I + 1>(addr, kx, ky, cj, cs);
+        } else {
+            spread_taps_rn<W, GS, J + 1, 0>(addr, kx, ky, cj, cs);
+        }
+    }
+}
+
+// Binary32 spreading of one cell's samples [q0, q1) into the fixed-point grid at word offset 0 of
+// `gaddr` (shared-memory address), conflict-free in the shared-memory banks.
+//
+// The 32 banks of a tap's address (base + j GS + i) differ between two samples exactly when their
+// base words differ modulo 32, so samples are scheduled by their class = base mod 32: per chunk of
+// CHUNK samples every thread prepares its samples (window, first node, kernel arguments, scaled
+// weight) and takes a slot in its class with a shared counter; the records are placed class by
+// class; then lane l of every warp spreads only class-l records (warp w takes rounds w, w + warps,
+// ...), so the 32 reductions of one instruction always hit 32 different banks.  Integer
+// reductions make the result independent of the order of the records.
+template <int NF, int W, int GS, int HO, int NT>
+__device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict__ srec, int* __restrict__ shist,
+                                                const FastFrame& ff, const float4* __restrict__ edge,
+                                                const CellConst& cc, const KernelPoly& kp,
+                                                const float* __restrict__ x, const float* __restrict__ y,
+                                                const float* __restrict__ h, const float* __restrict__ w, int64_t q0,
+                                                int64_t q1, float scale, unsigned* status) {
+    constexpr int K = kSpreadPerThread, CH = NT * K, NWARPS = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int par = 0;
+    for (int64_t c0 = q0; c0 < q1; c0 += CH, par ^= 1) {
+        int* hist = shist + 32 * par;
+        float px[K], py[K], ph[K], pw[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t q = c0 + tid + (int64_t)k * NT;
+            const bool in = q < q1;
+            px[k] = in ? x[q] : 0.0f;
+            py[k] = in ? y[q] : 0.0f;
+            ph[k] = in ? h[q] : 0.0f;
+            pw[k] = in ? w[q] : 0.0f;
+        }
+        int4 rec[K];
+        int cls[K], slot[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            cls[k] = -1;
+            slot[k] = 0;
+            rec[k] = make_int4(0, 0, 0, 0);
+            int r0x, r0y;
+            float ax, ay;
+            if (c0 + tid + (int64_t)k * NT < q1 &&
+                prep_coords_f32<NF, W>(ff, edge, cc, px[k], py[k], r0x, r0y, ax, ay, status)) {
+                const float cs = pw[k] * ph[k] * ff.inv_area * scale;
+                if (!isfinite(cs)) {
+                    atomicOr(status, ST_NONFINITE);
+                } else {
+                    const int word = (r0y + HO) * GS + (r0x + HO);
+                    cls[k] = word & 31;
+                    slot[k] = atomicAdd(&hist[cls[k]], 1);
+                    rec[k] = make_int4(word, __float_as_int(ax), __float_as_int(ay), __float_as_int(cs));
+                }
+            }
+        }
+        __syncthreads();   // every slot taken; the previous chunk's records are spread
+        if (warp == 0) shist[32 * (par ^ 1) + lane] = 0;   // the next chunk's counters
+        const int cnt = hist[lane];                         // lane l: class l
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int start = incl - cnt;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int st = __shfl_sync(0xffffffffu, start, cls[k] & 31);
+            if (cls[k] >= 0) srec[st + slot[k]] = rec[k];
+        }
+        int maxc = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+        __syncthreads();   // records in place
+        for (int r = warp; r < maxc; r += NWARPS) {
+            if (r < cnt) {
+                const int4 rc = srec[start + r];
+                float kx[W], ky[W];
+                kernel_pieces_sym<W>(kp, __int_as_float(rc.y), kx);
+                kernel_pieces_sym<W>(kp, __int_as_float(rc.z), ky);
+                spread_taps_rn<W, GS>(gaddr + 4u * (unsigned)rc.x, kx, ky, 0.0f, __int_as_float(rc.w));
+            }
         }
     }
 }
@@ -277,11 +422,12 @@ struct FixedRowPairAcc {
     }
 };
 
-// per-thread sum of |w_q h_q| / |D| over a cell's samples, reduced over the block (finite terms only)
+// per-thread sum and maximum of |w_q h_q| / |D| over a cell's samples, reduced over the block (finite
+// terms only); red holds 2 * NT / 32 floats
 template <int NT>
-__device__ __forceinline__ float cell_abs_sum(const float* __restrict__ h, const float* __restrict__ w, int64_t q0,
-                                              int64_t q1, float inv_area, float* red) {
-    float s = 0.0f;
+__device__ __forceinline__ float2 cell_abs_sum_max(const float* __restrict__ h, const float* __restrict__ w, int64_t q0,
+                                                   int64_t q1, float inv_area, float* red) {
+    float s = 0.0f, m = 0.0f;
     int64_t q = q0 + threadIdx.x;
     for (; q + 3 * NT < q1; q += 4 * NT) {   // four independent sample pairs in flight
         float hv[4], wv[4];
@@ -289,22 +435,35 @@ __device__ __forceinline__ float cell_abs_sum(const float* __restrict__ h, const
         for (int k = 0; k < 4; ++k) { hv[k] = h[q + k * NT]; wv[k] = w[q + k * NT]; }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float v = fabsf(wv[k] * hv[k]);
-            s += (v <= 3.0e38f) ? v : 0.0f;
+            float v = fabsf(wv[k] * hv[k]);
+            v = (v <= 3.0e38f) ? v : 0.0f;
+            s += v;
+            m = fmaxf(m, v);
         }
     }
     for (; q < q1; q += NT) {
-        const float v = fabsf(w[q] * h[q]);
-        s += (v <= 3.0e38f) ? v : 0.0f;
+        float v = fabsf(w[q] * h[q]);
+        v = (v <= 3.0e38f) ? v : 0.0f;
+        s += v;
+        m = fmaxf(m, v);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        red[NT / 32 + (threadIdx.x >> 5)] = m;
+    }
     __syncthreads();
-    float t = 0.0f;
+    float t = 0.0f, mx = 0.0f;
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) t += red[i];
-    return t * inv_area;
+    for (int i = 0; i < NT / 32; ++i) {
+        t += red[i];
+        mx = fmaxf(mx, red[NT / 32 + i]);
+    }
+    return make_float2(t * inv_area, mx * inv_area);
 }
 
 // contiguous complex workspace accessor
@@ -344,7 +503,8 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
     CellConst* scc = reinterpret_cast<CellConst*>(smem + CF::grid_bytes + CF::c1_bytes + CF::tw_bytes);
     int* sticket = reinterpret_cast<int*>(scc + 1);
     T* sinv = reinterpret_cast<T*>(sticket + 4);
-    float* sred = reinterpret_cast<float*>(sinv + kMaxHalf + 1);
+    float* sred = reinterpret_cast<float*>(sinv + kMaxHalf + 1);   // 2 * NWARPS floats
+    int* shist = reinterpret_cast<int*>(sred + 2 * CF::NWARPS);      // 2 x 32 class counters
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int P = a.P, half = P / 2, C1S = half + 1;
@@ -365,6 +525,7 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             float4* g4 = reinterpret_cast<float4*>(sgrid);
             const int n4 = (int)(CF::grid_bytes / 16);
             for (int i = tid; i < n4; i += CF::NT) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tid < 64) shist[tid] = 0;
         }
         __syncthreads();
         const CellConst& cc = *scc;
@@ -374,21 +535,15 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             int64_t q = q0 + tid;
             if constexpr (sizeof(T) == 4) {
                 const FastFrame ff = fast_frame(cc);
-                // fixed-point scale: every node of the grid is bounded by S = sum |c_q|
-                const float S = cell_abs_sum<CF::NT>(a.h, a.w, q0, q1, ff.inv_area, sred);
-                const float scale = S > 0x1p-96f ? 0x1p30f / S : 0x1p126f;
+                // fixed-point scale: every node of the grid is bounded by S = sum |c_q| (the kernel is
+                // <= 1), and every tap by max |c_q|; 2^30 / S keeps the nodes in 32 bits, 2^21 / max
+                // keeps each tap below 2^22, where one multiply-add rounds it to an integer
+                const float2 sm = cell_abs_sum_max<CF::NT>(a.h, a.w, q0, q1, ff.inv_area, sred);
+                const float scale = sm.x > 0x1p-96f ? fminf(0x1p30f / sm.x, 0x1p21f / sm.y) : 0x1p126f;
                 inv_scale = 1.0f / scale;
-                int* sgi = reinterpret_cast<int*>(sgrid);
-                // the next sample's loads are issued before the current one is spread
-                float x0 = 0.f, y0 = 0.f, h0 = 0.f, w0 = 0.f;
-                if (q < q1) { x0 = a.x[q]; y0 = a.y[q]; h0 = a.h[q]; w0 = a.w[q]; }
-                for (; q < q1; q += CF::NT) {
-                    const int64_t qn = q + CF::NT;
-                    float x1 = 0.f, y1 = 0.f, h1 = 0.f, w1 = 0.f;
-                    if (qn < q1) { x1 = a.x[qn]; y1 = a.y[qn]; h1 = a.h[qn]; w1 = a.w[qn]; }
-                    spread_f32<NF, W, GS, HO>(sgi, ff, cc.edge, cc, a.poly, x0, y0, h0, w0, scale, a.status);
-                    x0 = x1; y0 = y1; h0 = h1; w0 = w1;
-                }
+                spread_cell_f32<NF, W, GS, HO, CF::NT>((unsigned)__cvta_generic_to_shared(sgrid),
+                                                       reinterpret_cast<int4*>(sC1), shist, ff, cc.edge, cc,
+                                                       a.poly, a.x, a.y, a.h, a.w, q0, q1, scale, a.status);
             } else {
                 for (; q < q1; q += CF::NT)
                     spread_f64<NF, W, GS, HO>(sgrid, cc, a.poly, a.beta, a.x[q], a.y[q], a.h[q], a.w[q],

@@ -74,7 +74,7 @@ def _square(xs, ys, half=0.5):
     return synth.Workload(**{**wl.__dict__, "x": torch.tensor(xs, dtype=torch.float32),
                              "y": torch.tensor(ys, dtype=torch.float32), "h": torch.ones(n, dtype=torch.float32),
                              "w": torch.ones(n, dtype=torch.float32), "offsets": torch.tensor([0, n], dtype=torch.int64),
-                             "precision": "mixed"})
+                             "precision": "mixed", "width": 7, "tol": 0.0})
 
 
 @pytest.mark.parametrize("extra", [0, 17000])   # bucketed search; brute force (> 16384 windowed samples)
