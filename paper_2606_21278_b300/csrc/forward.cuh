@@ -282,6 +282,13 @@ __device__ __forceinline__ void spread_taps_rn(unsigned addr, const float (&kx)[
     }
 }
 
+// Ask L2 for the 128-byte lines of p[q0, q1): one prefetch per line (at an element inside the range),
+// spread over the block's threads.
+__device__ __forceinline__ void prefetch_l2(const float* __restrict__ p, int64_t q0, int64_t q1, int tid, int nt) {
+    for (int64_t q = q0 + (int64_t)tid * 32; q < q1; q += (int64_t)nt * 32)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + q));
+}
+
 // Binary32 spreading of one cell's samples [q0, q1) into the fixed-point grid at word offset 0 of
 // `gaddr` (shared-memory address), conflict-free in the shared-memory banks.
 //
@@ -355,6 +362,13 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
         __syncthreads();   // records in place
+        if (c0 + CH < q1) {   // the next chunk's samples toward L2 while this one is spread
+            const int64_t n0 = c0 + CH, n1 = min(q1, c0 + 2 * CH);
+            prefetch_l2(x, n0, n1, tid, NT);
+            prefetch_l2(y, n0, n1, tid, NT);
+            prefetch_l2(h, n0, n1, tid, NT);
+            prefetch_l2(w, n0, n1, tid, NT);
+        }
         for (int r = warp; r < maxc; r += NWARPS) {
             if (r < cnt) {
                 const int4 rc = srec[start + r];
@@ -512,12 +526,18 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
     for (int i = tid; i <= half; i += CF::NT) sinv[i] = a.inv_phi[i];
     float inv_scale = 1.0f;   // fixed-point scale of the current cell (binary32 path)
 
+    // tickets: the current cell and, one ahead, the next one (whose samples are requested toward L2
+    // while the current cell is transformed)
+    if (tid == 0) {
+        sticket[0] = (int)atomicAdd(a.ticket, 1u);
+        sticket[1] = (int)atomicAdd(a.ticket, 1u);
+    }
     for (;;) {
-        if (tid == 0) *sticket = (int)atomicAdd(a.ticket, 1u);
         __syncthreads();   // also orders the previous cell's last shared-memory reads
-        const int tk = *sticket;
+        const int tk = sticket[0], tkn = sticket[1];
         if (tk >= a.n_work) break;
         const int cell = a.order[tk];
+        const int ncell = tkn < a.n_work ? a.order[tkn] : -1;
         {   // per-cell constants into shared memory; zero the padded grid
             const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
             int4* dst = reinterpret_cast<int4*>(scc);
@@ -571,6 +591,15 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             sacc[rw * GS + c] += sacc[r * GS + c];
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            if (ncell >= 0) {   // the next cell's weights and elevations (its sum pass) and first samples
+                const int64_t n0 = a.offsets[ncell], n1 = a.offsets[ncell + 1];
+                prefetch_l2(a.h, n0, min(n1, n0 + 16384), tid, CF::NT);
+                prefetch_l2(a.w, n0, min(n1, n0 + 16384), tid, CF::NT);
+                prefetch_l2(a.x, n0, min(n1, n0 + CF::CHUNK), tid, CF::NT);
+                prefetch_l2(a.y, n0, min(n1, n0 + CF::CHUNK), tid, CF::NT);
+            }
+        }
         // ---- step 3a: FFT of the rows, two real rows per complex transform; keep m = 0..P/2
         {
             const int team = tid / N2, t = tid % N2;
@@ -617,6 +646,10 @@ type1_fused_kernel(const __grid_constant__ FwdArgs<T> a) {
             float4* d4 = reinterpret_cast<float4*>(a.coeffs + (size_t)cell * P * P * 2);
             const int n4 = P * P * (int)sizeof(cplx<T>) / 16;
             for (int i = tid; i < n4; i += CF::NT) d4[i] = s4[i];
+        }
+        if (tid == 0) {
+            sticket[0] = sticket[1];
+            sticket[1] = (int)atomicAdd(a.ticket, 1u);
         }
     }
 }
