@@ -404,6 +404,21 @@ def run_ours(args):
                  "bound": "hbm" if alg_all / (peak * 1e9) >= tc_flops / (tc_peak * 1e12) else "tensor",
                  "algorithmic_bytes": alg_all, "tensor_flops": tc_flops}
 
+    # the same step with the routes tuned at plan creation (threshold at most the workload's cap)
+    tuned = None
+    if not args.no_tune and info["cells_large"] == 0 and wl.x.dtype == torch.float32:
+        tplan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame, autotune=True)
+        tinfo = tplan.info()
+        tco = tplan.new_coeffs()
+        tout = tplan._ems_out(prm)
+        tg = _capture(lambda: tplan.type1_ems(wl.x, wl.y, wl.h, wl.w, prm, coeffs=tco, out=tout))
+        tms = _max_over_ranks(float(np.mean(_time_graph(tg, max(3, min(args.steps, 10))))), ws)
+        tplan.sync_status()
+        tuned = {"ms_per_step": tms, "value": pts_all / (tms * 1e-3), "unit": "points/s",
+                 "tuning": tplan.tuning(), "cells_tensor_core": tinfo["cells_tensor"],
+                 "cells_fused": tinfo["cells_fused"]}
+        del tg, tplan, tco, tout
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     hx, hy, hh, hw = (t.cpu().pin_memory() for t in (wl.x, wl.y, wl.h, wl.w))
     dx, dy, dh, dw = (torch.empty_like(t) for t in (wl.x, wl.y, wl.h, wl.w))
@@ -623,6 +638,7 @@ def run_ours(args):
                 "roofline": roof, "routes": routes, "step_roofline": step_roof, "cpu_baseline": cpu_base,
                 "e2e": {"value": pts_all / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
+                "tuned_routes": tuned,
                 "plain_fp32": plain,
                 "reconstruct": recon,
                 "voronoi": voronoi,
@@ -681,6 +697,7 @@ def main():
     ap.add_argument("--no-reconstruct", action="store_true", help="skip timing the reconstruction diagnostics")
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
     ap.add_argument("--no-gradient", action="store_true", help="skip timing the differentiation workload")
+    ap.add_argument("--no-tune", action="store_true", help="skip timing the step with tuned routes")
     ap.add_argument("--check-cells", type=int, default=1024,
                     help="cells of the untimed parity check against the binary64 oracle")
     ap.add_argument("--kernel", default="es", choices=["es", "kb"],

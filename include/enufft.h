@@ -101,6 +101,14 @@ typedef struct {
                              positive value return ENUFFT_ERR_UNSUPPORTED                       */
     enufft_kernel kernel; /* spreading kernel (default ES)                                       */
     enufft_frame frame;   /* local frame orientation (default CENTROID)                          */
+    int autotune;         /* 1: tune the execution routes at plan creation (see enufft_tuning):
+                             the tensor-core routing threshold, at most tc_max_points, and the
+                             fused kernel's blocks per SM; 0 (default): take tc_max_points as
+                             given.  Mixed-precision plans of the fused / tensor-core routes
+                             only; elsewhere it has no effect                                    */
+    const char *tune_cache;   /* NULL, or a JSON file of earlier tunings (read, and written on a
+                                 miss) keyed by GPU name, SM count, P, n_f, w, precision, kernel,
+                                 frame and tc_max_points                                        */
 } enufft_opts;
 
 typedef struct {
@@ -114,7 +122,7 @@ typedef struct {
 } enufft_ems_params;
 
 /* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path,
- * ES kernel, centroid-aligned frame. */
+ * ES kernel, centroid-aligned frame, no autotuning, no tuning cache. */
 void enufft_default_opts(enufft_opts *opts);
 /* Defaults of the paper's EMS illustration (Sec. 2.2): K_min 1, K_max 12, alpha 0..0.7,
  * delta 0.02, w1 = w2 = 0.5, HEAD sums, DC excluded. */
@@ -290,8 +298,41 @@ typedef struct {
     int64_t cells_plain, kernels_per_type1_ems;
     int kernel;                        /* enufft_kernel of the plan                             */
     int frame;                         /* enufft_frame of the plan                              */
+    int tc_max_points;                 /* routing threshold in effect (tuned or as given)       */
+    int autotuned;                     /* 1 if the routes were tuned at plan creation           */
+    int fused_blocks_per_sm;           /* persistent blocks per SM of the fused kernel          */
 } enufft_plan_info;
 enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
+
+/*
+ * Route tuning (the paper has no counterpart; it is part of running the batched method well on this
+ * hardware).  With opts.autotune = 1 the plan times, on synthetic batches drawn from its own cells
+ * (each synthetic cell copies the frame of a plan cell, with Q samples spread uniformly over its
+ * window), the fused spread/FFT kernel against the tensor-core direct sum at Q = 128, 256, 512,
+ * 1024, 2048, 3072, 4096, 6144 (those not above tc_max_points) and keeps as threshold the largest Q
+ * at which the direct sum was faster per sample (0 = none); and the fused kernel with one against
+ * two resident blocks per SM, at the plan's median cell size.  Results are identical either way
+ * within the accuracy of each route; only the time changes.
+ *   ladder[i], ns_fused[i], ns_tc[i]: the measured ns per sample of each route at Q = ladder[i]
+ *   from_cache: 1 if the record was read from opts.tune_cache instead of measured
+ */
+typedef struct {
+    int tc_max_points;
+    int fused_blocks_per_sm;
+    int n_ladder;
+    int ladder[8];
+    double ns_fused[8];
+    double ns_tc[8];
+    int from_cache;
+} enufft_tuning;
+/* The plan's tuning record; ENUFFT_ERR_ARG if the plan was not tuned. */
+enufft_status enufft_get_tuning(enufft_plan plan, enufft_tuning *out);
+/* Host-only access to a tuning cache file (no GPU needed): look up the record of `key`
+ * (ENUFFT_OK, or ENUFFT_ERR_ARG when the file is missing or malformed or has no such key), and
+ * store one (the file is created, or rewritten with the key added or replaced; a malformed file is
+ * replaced; keys may not contain '"' or '\\'). */
+enufft_status enufft_tune_cache_lookup(const char *path, const char *key, enufft_tuning *out);
+enufft_status enufft_tune_cache_store(const char *path, const char *key, const enufft_tuning *t);
 
 #ifdef __cplusplus
 }

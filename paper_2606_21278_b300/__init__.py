@@ -13,7 +13,8 @@ from dataclasses import dataclass
 
 import torch
 
-__all__ = ["Plan", "EMSParams", "EMSRetainedPower", "load_library", "LIB_PATH", "EnufftError"]
+__all__ = ["Plan", "EMSParams", "EMSRetainedPower", "load_library", "LIB_PATH", "EnufftError", "tune_cache_lookup",
+           "tune_cache_store"]
 
 LIB_PATH = os.environ.get("ENUFFT_LIB", os.path.join(os.path.dirname(os.path.abspath(__file__)), "libenufft.so"))
 _lib = None
@@ -32,7 +33,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("oversamp", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("tol", ctypes.c_double), ("prec", ctypes.c_int), ("mask", ctypes.c_int),
                 ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("frame", ctypes.c_int)]
+                ("frame", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 class _Ems(ctypes.Structure):
@@ -47,7 +48,21 @@ class _Info(ctypes.Structure):
                 ("n_cells", ctypes.c_int64), ("n_points", ctypes.c_int64), ("cells_fused", ctypes.c_int64),
                 ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64),
-                ("kernel", ctypes.c_int), ("frame", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("frame", ctypes.c_int), ("tc_max_points", ctypes.c_int),
+                ("autotuned", ctypes.c_int), ("fused_blocks_per_sm", ctypes.c_int)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("tc_max_points", ctypes.c_int), ("fused_blocks_per_sm", ctypes.c_int), ("n_ladder", ctypes.c_int),
+                ("ladder", ctypes.c_int * 8), ("ns_fused", ctypes.c_double * 8), ("ns_tc", ctypes.c_double * 8),
+                ("from_cache", ctypes.c_int)]
+
+
+def _tuning_dict(t: _Tuning) -> dict:
+    n = t.n_ladder
+    return {"tc_max_points": t.tc_max_points, "fused_blocks_per_sm": t.fused_blocks_per_sm,
+            "ladder": list(t.ladder[:n]), "ns_fused": list(t.ns_fused[:n]), "ns_tc": list(t.ns_tc[:n]),
+            "from_cache": bool(t.from_cache)}
 
 
 def load_library(path: str = LIB_PATH):
@@ -79,10 +94,13 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint]
     lib.enufft_reconstruct.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
     lib.enufft_voronoi_weights.argtypes = [vp, vp, vp, i32, vp]
+    lib.enufft_get_tuning.argtypes = [vp, P(_Tuning)]
+    lib.enufft_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P(_Tuning)]
+    lib.enufft_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P(_Tuning)]
     for f in ("enufft_plan_create", "enufft_plan_destroy", "enufft_type1", "enufft_ems", "enufft_type1_ems",
               "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status", "enufft_set_stream",
               "enufft_get_plan_info", "enufft_selftest_wait_timeout", "enufft_reconstruct",
-              "enufft_voronoi_weights"):
+              "enufft_voronoi_weights", "enufft_get_tuning", "enufft_tune_cache_lookup", "enufft_tune_cache_store"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -120,7 +138,7 @@ class Plan:
     def __init__(self, offsets: torch.Tensor, nverts: torch.Tensor, verts: torch.Tensor, modes: int = 64,
                  oversamp: float = 2.0, kernel_width: int = 7, tol: float = 0.0, precision: str = "mixed",
                  mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0, kernel: str = "es",
-                 frame: str | int = "centroid"):
+                 frame: str | int = "centroid", autotune: bool = False, tune_cache: str | None = None):
         self._lib = load_library()
         if not torch.cuda.is_available():
             raise EnufftError("no CUDA device")
@@ -139,7 +157,8 @@ class Plan:
             raise EnufftError(f"frame must be one of {sorted(_FRAME)}")
         o = _Opts(modes, oversamp, kernel_width, tol, _PREC[precision],
                   _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points, _KERNEL[kernel],
-                  _FRAME[frame] if isinstance(frame, str) else int(frame))
+                  _FRAME[frame] if isinstance(frame, str) else int(frame), int(bool(autotune)),
+                  tune_cache.encode() if tune_cache else None)
         h = ctypes.c_void_p()
         st = self._lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), self.n_cells, _ptr(self.offsets),
                                           _ptr(self.nverts), _ptr(self.verts), _stream())
@@ -181,6 +200,12 @@ class Plan:
         i = _Info()
         self._check(self._lib.enufft_get_plan_info(self._h, ctypes.byref(i)), "get_plan_info")
         return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def tuning(self) -> dict:
+        """The plan's route tuning record (see enufft_get_tuning); raises if the plan was not tuned."""
+        t = _Tuning()
+        self._check(self._lib.enufft_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        return _tuning_dict(t)
 
     def voronoi_weights(self, x, y, ng: int = 64) -> torch.Tensor:
         """Voronoi quadrature weights by raster sampling (see enufft_voronoi_weights)."""
@@ -299,3 +324,28 @@ class EMSRetainedPower(torch.autograd.Function):
         g = plan.ems_backward(coeffs, ks, sel, grad_power, ctx.params, ctx.mw)
         gh, gw = plan.type1_backward(g, x, y, h.detach(), w.detach(), ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         return gh, gw, None, None, None, None, None
+
+
+def tune_cache_lookup(path: str, key: str) -> dict | None:
+    """The record of `key` in a tuning cache file, or None (see enufft_tune_cache_lookup)."""
+    lib = load_library()
+    t = _Tuning()
+    if lib.enufft_tune_cache_lookup(path.encode(), key.encode(), ctypes.byref(t)) != 0:
+        return None
+    return _tuning_dict(t)
+
+
+def tune_cache_store(path: str, key: str, rec: dict) -> None:
+    """Store a tuning record under `key` (see enufft_tune_cache_store)."""
+    lib = load_library()
+    t = _Tuning()
+    t.tc_max_points = int(rec["tc_max_points"])
+    t.fused_blocks_per_sm = int(rec["fused_blocks_per_sm"])
+    n = len(rec.get("ladder", []))
+    t.n_ladder = n
+    for i in range(n):
+        t.ladder[i] = int(rec["ladder"][i])
+        t.ns_fused[i] = float(rec["ns_fused"][i])
+        t.ns_tc[i] = float(rec["ns_tc"][i])
+    if lib.enufft_tune_cache_store(path.encode(), key.encode(), ctypes.byref(t)) != 0:
+        raise EnufftError(f"tune_cache_store: {lib.enufft_last_error(None).decode()}")

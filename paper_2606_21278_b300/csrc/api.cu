@@ -87,6 +87,10 @@ struct enufft_plan_s {
     EmsScratch ems_scratch = {nullptr, nullptr};   // stage-1 EMS results per cell
     void* d_twiddle = nullptr;
     int fwd_per_sm = 0, adj_per_sm = 0;
+    int fwd_grid_per_sm = 0;         // persistent fused blocks launched per SM (tuned or fwd_per_sm)
+    int tc_threshold = 0;            // routing threshold in effect
+    bool tuned = false;
+    enufft_tuning tuning = {};
     double inv_phi[kMaxHalf + 1] = {};
     KernelPoly poly = {};
     // large-grid (n_f = 256) route: cells in batches with bounded scratch
@@ -269,6 +273,8 @@ void enufft_default_opts(enufft_opts* o) {
     o->tc_max_points = 0;
     o->kernel = ENUFFT_KERNEL_ES;
     o->frame = ENUFFT_FRAME_CENTROID;
+    o->autotune = 0;
+    o->tune_cache = nullptr;
 }
 
 void enufft_default_ems(enufft_ems_params* p) {
@@ -344,6 +350,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad kernel");
     if (o.frame != ENUFFT_FRAME_CENTROID && o.frame != ENUFFT_FRAME_EDGE)
         return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad frame");
+    if (o.autotune != 0 && o.autotune != 1) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: autotune must be 0 or 1");
 
     enufft_plan p = new enufft_plan_s();
     p->opts = o;
@@ -477,6 +484,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         for (int64_t j = 0; j < n_cells; ++j)
             if (off[j + 1] - off[j] <= o.tc_max_points) ++p->n_tc;
         p->n_fused = (int)(n_cells - p->n_tc);
+        p->tc_threshold = o.tc_max_points;
     }
     if (n_cells > 0) {
         e = cudaMemcpyAsync(p->d_order, order.data(), sizeof(int) * n_cells, cudaMemcpyHostToDevice, p->stream);
@@ -591,7 +599,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         *out = p;
         return ENUFFT_OK;
     }
-    if (p->n_tc > 0 && (e = tc_prepare()) != cudaSuccess) {
+    if ((p->n_tc > 0 || (o.autotune && o.tc_max_points > 0)) && (e = tc_prepare()) != cudaSuccess) {
         enufft_status st = cuda_fail(nullptr, e, "plan_create: tensor-core kernel attributes");
         enufft_plan_destroy(p);
         return st;
@@ -603,7 +611,50 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         enufft_plan_destroy(p);
         return st;
     }
+    p->fwd_grid_per_sm = p->fwd_per_sm;
+    if (o.autotune && !p->dbl && n_cells > 0) {
+        // key: the configuration on this kind of GPU
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, p->device);
+        std::string gpu = prop.name;
+        for (char& c : gpu)
+            if (c == '"' || c == '\\') c = '_';
+        char key[384];
+        snprintf(key, sizeof key, "gpu=%s|sms=%d|P=%d|nf=%d|w=%d|prec=%d|kernel=%d|frame=%d|tc_cap=%d", gpu.c_str(),
+                 p->num_sms, p->P, NF, W, (int)o.prec, (int)o.kernel, (int)o.frame, o.tc_max_points);
+        enufft_tuning t;
+        if (!(o.tune_cache && tune_cache_get(o.tune_cache, key, &t))) {
+            std::vector<int64_t> q(n_cells);
+            for (int64_t j = 0; j < n_cells; ++j) q[j] = off[j + 1] - off[j];
+            std::nth_element(q.begin(), q.begin() + n_cells / 2, q.end());
+            TuneEnv env{p->d_cells, (int)n_cells, p->P, NF, W, p->poly, p->beta, p->inv_phi, p->d_twiddle,
+                        p->num_sms, p->fwd_per_sm, p->d_ctr + 2, p->stream, o.tc_max_points,
+                        (int)std::min<int64_t>(q[n_cells / 2], 1 << 20)};
+            if ((e = autotune_run(env, &t)) != cudaSuccess) {
+                enufft_status st = cuda_fail(nullptr, e, "plan_create: autotune");
+                enufft_plan_destroy(p);
+                return st;
+            }
+            if (o.tune_cache) tune_cache_put(o.tune_cache, key, t);   // best effort: an unwritable cache is skipped
+        }
+        p->tuned = true;
+        p->tuning = t;
+        p->fwd_grid_per_sm = std::max(1, std::min(t.fused_blocks_per_sm, p->fwd_per_sm));
+        p->tc_threshold = std::min(t.tc_max_points, o.tc_max_points);
+        p->n_tc = 0;
+        if (p->tc_threshold > 0)
+            for (int64_t j = 0; j < n_cells; ++j)
+                if (off[j + 1] - off[j] <= p->tc_threshold) ++p->n_tc;
+        p->n_fused = (int)(n_cells - p->n_tc);
+    }
     *out = p;
+    return ENUFFT_OK;
+}
+
+enufft_status enufft_get_tuning(enufft_plan p, enufft_tuning* out) {
+    if (!p || !out) return fail(p, ENUFFT_ERR_ARG, "get_tuning: NULL argument");
+    if (!p->tuned) return fail(p, ENUFFT_ERR_ARG, "get_tuning: the plan was not tuned");
+    *out = p->tuning;
     return ENUFFT_OK;
 }
 
@@ -623,6 +674,9 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->cells_plain = p->plain ? p->n_cells : 0;
     info->kernel = (int)p->opts.kernel;
     info->frame = (int)p->opts.frame;
+    info->tc_max_points = p->n_tc > 0 || p->tuned ? p->tc_threshold : 0;
+    info->autotuned = p->tuned ? 1 : 0;
+    info->fused_blocks_per_sm = p->fwd_grid_per_sm;
     int64_t k = 0;
     if (p->plain) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
@@ -855,7 +909,7 @@ static enufft_status run_type1(enufft_plan p, const void* x, const void* y, cons
     if (a.n_work > 0) {
         e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned), p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1: memset");
-        const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_per_sm * p->num_sms);
+        const int grid = std::min<int64_t>(a.n_work, (int64_t)p->fwd_grid_per_sm * p->num_sms);
         e = launch_type1(a, p->NF, p->W, grid, p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1: launch");
     }

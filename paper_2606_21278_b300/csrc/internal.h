@@ -5,6 +5,7 @@
 
 #include <string>
 
+#include "enufft.h"
 #include "adjoint.cuh"
 #include "forward.cuh"
 
@@ -80,6 +81,25 @@ cudaError_t launch_tc_nudft(const TcLaunch& l, cudaStream_t s);
 // Voronoi quadrature weights by raster sampling (voronoi.cu), binary32 samples.
 cudaError_t launch_voronoi(const float* x, const float* y, const int64_t* offsets, const CellConst* cells, int n_cells,
                            int Ng, float* w, unsigned* status, int num_sms, cudaStream_t s);
+
+// Plan-time route tuning (autotune.cu).
+struct TuneEnv {
+    const CellConst* cells;   // the plan's cells (device)
+    int n_cells;
+    int P, NF, W;
+    KernelPoly poly;
+    double beta;
+    const double* inv_phi;    // host, P/2 + 1 entries
+    const void* twiddle;      // device
+    int num_sms, fwd_per_sm;  // SMs; resident fused blocks per SM
+    unsigned* status;
+    cudaStream_t stream;
+    int tc_cap;               // largest cell size the caller allows on the tensor cores (0: none)
+    int q_median;             // the plan's median cell size
+};
+cudaError_t autotune_run(const TuneEnv& env, enufft_tuning* out);
+bool tune_cache_get(const char* path, const std::string& key, enufft_tuning* out);
+bool tune_cache_put(const char* path, const std::string& key, const enufft_tuning& t);
 
 // Record the calling thread's last error text (read back by enufft_last_error(NULL)).
 void set_thread_error(const std::string& msg);

@@ -50,8 +50,8 @@ def test_build_targets_sm_103a_only():
 def test_defaults(lib):
     o = enufft._Opts()
     lib.enufft_default_opts(ctypes.byref(o))
-    assert (o.modes, o.oversamp, o.kernel_width, o.prec, o.mask, o.eta, o.tc_max_points, o.kernel, o.frame) == \
-        (64, 2.0, 7, 2, 0, 1.5, 0, 0, 0)
+    assert (o.modes, o.oversamp, o.kernel_width, o.prec, o.mask, o.eta, o.tc_max_points, o.kernel, o.frame,
+            o.autotune, o.tune_cache) == (64, 2.0, 7, 2, 0, 1.5, 0, 0, 0, 0, None)
     e = enufft._Ems()
     lib.enufft_default_ems(ctypes.byref(e))
     assert (e.k_min, e.k_max, e.alpha_min, e.alpha_max, e.delta, e.w1, e.w2, e.sum_over, e.include_dc) == \
@@ -106,3 +106,33 @@ def test_binding_option_maps_match_the_header():
         assert set(table) == set(names)
         for key, cname in names.items():
             assert table[key] == values[cname], (key, cname)
+
+
+def test_tune_cache_round_trip(tmp_path, lib):
+    """The tuning cache file (enufft_tune_cache_store / _lookup, host only): records round-trip with
+    their timings, keys coexist and are replaced, a missing key, a missing file and a malformed file
+    are misses, a malformed file is replaced by the next store, and the file is plain JSON."""
+    import json
+    path = str(tmp_path / "tune.json")
+    a = {"tc_max_points": 512, "fused_blocks_per_sm": 2, "ladder": [128, 256, 512, 1024],
+         "ns_fused": [0.31, 0.16, 0.09, 0.05], "ns_tc": [0.2, 0.15, 0.08, 0.07]}
+    b = {"tc_max_points": 0, "fused_blocks_per_sm": 1, "ladder": [], "ns_fused": [], "ns_tc": []}
+    assert enufft.tune_cache_lookup(path, "k1") is None                       # no file yet
+    enufft.tune_cache_store(path, "gpu=X|P=64", a)
+    enufft.tune_cache_store(path, "gpu=X|P=32", b)
+    got = enufft.tune_cache_lookup(path, "gpu=X|P=64")
+    assert got["tc_max_points"] == 512 and got["fused_blocks_per_sm"] == 2 and got["ladder"] == a["ladder"]
+    assert got["ns_fused"] == pytest.approx(a["ns_fused"], rel=1e-5) and got["ns_tc"] == pytest.approx(a["ns_tc"], rel=1e-5)
+    assert got["from_cache"] is True
+    assert enufft.tune_cache_lookup(path, "gpu=X|P=32")["tc_max_points"] == 0
+    assert enufft.tune_cache_lookup(path, "gpu=Y|P=64") is None
+    enufft.tune_cache_store(path, "gpu=X|P=64", {**a, "tc_max_points": 1024})  # replaced, not duplicated
+    d = json.load(open(path))
+    assert sorted(d) == ["gpu=X|P=32", "gpu=X|P=64"] and d["gpu=X|P=64"]["tc_max_points"] == 1024
+    open(path, "w").write("{not json")
+    assert enufft.tune_cache_lookup(path, "gpu=X|P=64") is None
+    enufft.tune_cache_store(path, "k", b)
+    assert json.load(open(path)) == {"k": {"tc_max_points": 0, "fused_blocks_per_sm": 1, "ladder": [],
+                                           "ns_fused": [], "ns_tc": []}}
+    with pytest.raises(enufft.EnufftError):
+        enufft.tune_cache_store(path, 'bad"key', b)
