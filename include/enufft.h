@@ -199,6 +199,9 @@ enufft_status enufft_ems_backward(enufft_plan plan, const void *d_coeffs, const 
  *   d_grad_h       [N] dL/dh_q = win_q w_q v_q / |D|     (may be NULL)
  *   d_grad_w       [N] dL/dw_q = win_q h_q v_q / |D|     (may be NULL)
  *   with v_q = Re sum_mn G_mn exp(+i (k_m x'_q + k_n y'_q)).
+ * Every route: the fused adjoint kernel for n_f <= 128 (cells of the tensor-core route included),
+ * two kernels per batch for n_f = 256 (inverse transforms into the batch's fine grids, then
+ * interpolation from staged windows of them).  Plain FP32 plans return ENUFFT_ERR_UNSUPPORTED.
  */
 enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs, const void *d_x,
                                     const void *d_y, const void *d_h, const void *d_w, void *d_grad_h,
@@ -210,8 +213,10 @@ enufft_status enufft_type1_backward(enufft_plan plan, const void *d_grad_coeffs,
  * ENUFFT_ERR_UNSUPPORTED):
  *   - raster points at the centres of an ng x ng grid over the cell's square B, kept when inside
  *     the window (the plan's mask);
- *   - each kept point goes to its nearest windowed sample (squared distance in binary32, every
- *     operation rounded as written, ties to the lowest sample index); n_q counts its points;
+ *   - each kept point goes to its nearest windowed sample (Eq. nn_assignment: the squared
+ *     distance in binary64, every operation rounded as written, ties to the lowest sample index;
+ *     the search runs in binary32 and re-decides in binary64 where the binary32 gap to the
+ *     second-nearest sample is within its certified rounding bound); n_q counts its points;
  *   - d_w[q] = max(n_q, 1/2) |D| / sum_q' max(n_q', 1/2) (a sample no point reached takes the
  *     floor 1/2; the weights of a cell sum to |D|), 0 for samples outside the window.
  * d_w [N] binary32 (caller-owned) is also the count scratch while the call runs.  ng in [2, 1024];
@@ -233,8 +238,9 @@ enufft_status enufft_voronoi_weights(enufft_plan plan, const void *d_x, const vo
  *   d_stats[4 j + 2] sigma2_spec over the selected set, (m, n) != (0, 0)
  *   d_stats[4 j + 3] sigma2_spec over the whole P x P box, (m, n) != (0, 0)   (Eq. spectral_variance)
  * The paper evaluates these on deplaned elevations (h minus the cell's weighted mean); the call
- * uses h as given.  k_max is the row length of d_sel (1..64).  Not built for n_f = 256 and plain
- * plans (ENUFFT_ERR_UNSUPPORTED); NULL pointers or a bad k_max return ENUFFT_ERR_ARG.
+ * uses h as given.  k_max is the row length of d_sel (1..64).  Built on the adjoint's kernels of
+ * each route; plain FP32 plans return ENUFFT_ERR_UNSUPPORTED; NULL pointers or a bad k_max return
+ * ENUFFT_ERR_ARG.
  */
 enufft_status enufft_reconstruct(enufft_plan plan, const void *d_coeffs, const int32_t *d_kstar,
                                  const int32_t *d_sel, int k_max, const void *d_x, const void *d_y,

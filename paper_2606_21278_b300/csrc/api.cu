@@ -19,6 +19,7 @@
 #include "internal.h"
 #include "kernels_misc.cuh"
 #include "large_args.cuh"
+#include "large_adj.cuh"
 
 using namespace enufft;
 
@@ -108,6 +109,8 @@ struct enufft_plan_s {
     float4* d_lrec = nullptr;
     unsigned long long* d_lgrid = nullptr;   // fixed-point fine grids of one batch
     int* d_lexp = nullptr;                   // their scales
+    double* d_lpartial = nullptr;            // reconstruction: per work item partial sums [max items][3]
+    double* d_lspec = nullptr;               // reconstruction: per cell spectral variances [n_cells][2]
     int lmax_cells = 0;
     // edge-aligned frame: per-cell centroid and rotation, per-call local coordinates of the samples
     bool edge = false;
@@ -313,6 +316,8 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_lrec);
     cudaFree(p->d_lgrid);
     cudaFree(p->d_lexp);
+    cudaFree(p->d_lpartial);
+    cudaFree(p->d_lspec);
     cudaFree(p->d_pgrid);
     cudaFree(p->d_pbuf);
     cudaFree(p->d_rot);
@@ -532,6 +537,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         std::vector<int2> cellblk(std::max<int64_t>(n_cells, 1));
         int64_t max_pts = 0;
         int max_blocks = 0;
+        size_t max_work = 0;
         for (int64_t c = 0; c < n_cells;) {
             enufft_plan_s::LBatch b{(int)c, 0, (int)blocks.size(), 0, 0, 0, off[c]};
             while (c < n_cells && b.ncells < kLargeBatchCells &&
@@ -557,6 +563,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
                 for (int k = 0; k < parts; ++k) work.push_back(make_int4(u, k, parts, 0));
             }
             b.nwork = (int)work.size() - b.work0;
+            max_work = std::max(max_work, (size_t)b.nwork);
             max_pts = std::max<int64_t>(max_pts, off[c] - b.p0);
             max_blocks = std::max(max_blocks, b.nblocks);
             p->lmax_cells = std::max(p->lmax_cells, b.ncells);
@@ -574,7 +581,9 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
             (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTiles * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lgrid, sizeof(unsigned long long) * kLNF * kLNF * mc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_lexp, sizeof(int) * mc)) != cudaSuccess) {
+            (e = cudaMalloc(&p->d_lexp, sizeof(int) * mc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lpartial, sizeof(double) * 3 * std::max<size_t>(max_work, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lspec, sizeof(double) * 2 * std::max<int64_t>(n_cells, 1))) != cudaSuccess) {
             enufft_status st = cuda_fail(nullptr, e, "plan_create: large-route scratch");
             enufft_plan_destroy(p);
             return st;
@@ -1007,9 +1016,56 @@ enufft_status enufft_ems_backward(enufft_plan p, const void* d_coeffs, const dou
 
 }  // extern "C"
 
+// adjoint / reconstruction of the n_f = 256 route, batch by batch (large_adj.cuh)
+static enufft_status run_adjoint_large(enufft_plan p, const void* g, const void* x, const void* y, const void* h,
+                                       const void* w, void* gh, void* gw, const AdjArgs<float>* recon) {
+    LargeAdjFftArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.gcoef = (const float*)g;
+    fa.mode = recon ? 1 : 0;
+    fa.P = p->P;
+    fa.grid = reinterpret_cast<float*>(p->d_lgrid);
+    fa.spec = p->d_lspec;
+    fa.twiddle = (const cplx<float>*)p->d_twiddle;
+    for (int k = 0; k <= p->P / 2; ++k) fa.inv_phi[k] = (float)p->inv_phi[k];
+    LargeInterpArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.x = (const float*)x;
+    ia.y = (const float*)y;
+    ia.h = (const float*)h;
+    ia.w = (const float*)w;
+    ia.offsets = p->d_offsets;
+    ia.cells = p->d_cells;
+    ia.grid = fa.grid;
+    ia.mode = fa.mode;
+    ia.grad_h = (float*)gh;
+    ia.grad_w = (float*)gw;
+    ia.partial = p->d_lpartial;
+    ia.status = p->d_ctr + 2;
+    ia.poly = p->poly;
+    if (recon) {
+        fa.kstar = recon->kstar;
+        fa.sel = recon->sel;
+        fa.k_max = recon->k_max;
+        ia.hrec = recon->hrec;
+    }
+    for (const auto& b : p->lbatches) {
+        fa.cell0 = ia.cell0 = b.cell0;
+        fa.ncells = b.ncells;
+        ia.work = p->d_lwork + b.work0;
+        cudaError_t e = large_run_adjoint_batch(fa, ia, b.nwork, p->W, std::min(b.ncells, p->num_sms),
+                                                recon ? recon->stats : nullptr, p->d_cells, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "adjoint (large): launch");
+    }
+    return ENUFFT_OK;
+}
+
 template <typename T>
 static enufft_status run_adjoint(enufft_plan p, const void* g, const void* x, const void* y, const void* h,
                                  const void* w, void* gh, void* gw, const AdjArgs<T>* recon = nullptr) {
+    if constexpr (sizeof(T) == 4) {
+        if (p->large) return run_adjoint_large(p, g, x, y, h, w, gh, gw, recon);
+    }
     AdjArgs<T> a;
     memset(&a, 0, sizeof(a));
     if (recon) a = *recon;
@@ -1077,7 +1133,6 @@ extern "C" enufft_status enufft_reconstruct(enufft_plan p, const void* d_coeffs,
     if (!d_coeffs || !d_kstar || !d_sel || !d_stats || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
         return fail(p, ENUFFT_ERR_ARG, "reconstruct: NULL data pointer");
     if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "reconstruct: coeffs must be 16-byte aligned");
-    if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for n_f = 256 plans");
     if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "reconstruct: not built for plain FP32 plans");
     cudaSetDevice(p->device);
     const enufft_status es = edge_prepass(p, d_x, d_y);
@@ -1094,7 +1149,6 @@ extern "C" enufft_status enufft_type1_backward(enufft_plan p, const void* d_grad
     if (!d_grad_coeffs || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
         return fail(p, ENUFFT_ERR_ARG, "type1_backward: NULL data pointer");
     if (!aligned16(d_grad_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_backward: grad_coeffs must be 16-byte aligned");
-    if (p->large) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for n_f = 256 plans");
     if (p->plain) return fail(p, ENUFFT_ERR_UNSUPPORTED, "type1_backward: not built for plain FP32 plans");
     cudaSetDevice(p->device);
     const enufft_status es = edge_prepass(p, d_x, d_y);

@@ -1,12 +1,47 @@
 // inst_large.cu -- launchers of the large-grid (n_f = 256) pipeline.
 #include "internal.h"
 #include "large.cuh"
+#include "large_adj.cuh"
 
 namespace enufft {
 
+template <int W>
+static cudaError_t interp_attr() {
+    return cudaFuncSetAttribute(large_interp_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLInterpSmem);
+}
+
 cudaError_t large_prepare(int P) {
-    return cudaFuncSetAttribute(large_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)large_fft_smem_bytes(P));
+    cudaError_t e = cudaFuncSetAttribute(large_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)large_fft_smem_bytes(P));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(large_adj_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)large_adj_fft_smem_bytes(P));
+    if (e == cudaSuccess) e = interp_attr<4>();
+    if (e == cudaSuccess) e = interp_attr<5>();
+    if (e == cudaSuccess) e = interp_attr<6>();
+    if (e == cudaSuccess) e = interp_attr<7>();
+    if (e == cudaSuccess) e = interp_attr<8>();
+    return e;
+}
+
+cudaError_t large_run_adjoint_batch(const LargeAdjFftArgs& fa, const LargeInterpArgs& ia, int nwork, int W,
+                                    int fft_grid, double* stats, const CellConst* cells, cudaStream_t s) {
+    if (fa.ncells <= 0) return cudaSuccess;
+    large_adj_fft_kernel<<<fft_grid, kLAdjThreads, large_adj_fft_smem_bytes(fa.P), s>>>(fa);
+    if (nwork > 0) {
+        switch (W) {
+            case 4: large_interp_kernel<4><<<nwork, kLAdjThreads, kLInterpSmem, s>>>(ia); break;
+            case 5: large_interp_kernel<5><<<nwork, kLAdjThreads, kLInterpSmem, s>>>(ia); break;
+            case 6: large_interp_kernel<6><<<nwork, kLAdjThreads, kLInterpSmem, s>>>(ia); break;
+            case 7: large_interp_kernel<7><<<nwork, kLAdjThreads, kLInterpSmem, s>>>(ia); break;
+            case 8: large_interp_kernel<8><<<nwork, kLAdjThreads, kLInterpSmem, s>>>(ia); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (fa.mode == 1)
+        large_recon_stats_kernel<<<(fa.ncells + 127) / 128, 128, 0, s>>>(fa.cell0, fa.ncells, ia.work, nwork, ia.partial,
+                                                                        fa.spec, cells, stats);
+    return cudaGetLastError();
 }
 
 template <int W>

@@ -42,6 +42,12 @@ struct LargeFftArgs;
 cudaError_t large_prepare(int P);
 cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
                             int fft_grid, cudaStream_t s);
+struct LargeAdjFftArgs;
+struct LargeInterpArgs;
+// adjoint (mode 0) or reconstruction (mode 1) of one batch: per-cell inverse transforms into the
+// batch's fine grids, interpolation per work item, and (mode 1) the per-cell diagnostics
+cudaError_t large_run_adjoint_batch(const LargeAdjFftArgs& fa, const LargeInterpArgs& ia, int nwork, int W,
+                                    int fft_grid, double* stats, const CellConst* cells, cudaStream_t s);
 
 // Plain binary32 per-cell path (plain.cu): one launch sequence per cell.
 struct PlainRun {
