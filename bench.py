@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "NU points/s, batched type-1 ENUFFT+EMS at rel-l2<=1e-5; mixed vs plain FP32, 1 B300"
+# compute peaks of this GPU from `python bench.py --peaks` (enufft_probe_peaks): binary32 FMA TFLOP/s
+# and conflict-free shared-memory 32-bit reductions per second (1e9) over all SMs
+FP32_TFLOPS = 70.9
+SMEM_RED_GOPS = 9120.0
 DEFAULT_WORKLOAD = "tri81920_p64_mixed"
 KERNEL_SOURCES = ["common.cuh", "fft.cuh", "ems.cuh", "forward.cuh", "inst_common.cuh", "inst_f32_128.cu"]
 
@@ -396,6 +400,25 @@ def run_ours(args):
             "traffic": _traffic(args.workload) if args.frame == "centroid" else None, "peak_source": peak_src,
             "kernel": kern, "algorithmic_bytes_per_launch": routes["fused"]["hbm"]["algorithmic_bytes_per_launch"]
             if "fused" in routes else alg_all}
+    # the fused kernel's other bounds: its algorithmic binary32 arithmetic against the FP32 peak, and
+    # its w^2 shared-memory reductions per sample against the conflict-free reduction rate (both
+    # measured by enufft_probe_peaks; the figures of the last probe are kept below)
+    if "fused" in routes and info["cells_large"] == 0:
+        fr = routes["fused"]
+        Wd = info["kernel_width"]
+        nf = info["fine_grid"]
+        flops = (12 * Wd + Wd + 2 * Wd * Wd) * fr["points"] + \
+            (2.5 * nf * nf * math.log2(nf * nf) + 2 * P * P + 4 * P * P // 2) * fr["cells"]
+        t_hbm = fr["hbm"]["algorithmic_bytes_per_launch"] / (peak * 1e9)
+        t_alu = flops / (FP32_TFLOPS * 1e12)
+        t_red = Wd * Wd * fr["points"] / (SMEM_RED_GOPS * 1e9)
+        t_bind = max(t_hbm, t_alu, t_red)
+        fr["roofline_terms"] = {
+            "hbm_ms": 1e3 * t_hbm, "alu_fp32_ms": 1e3 * t_alu, "smem_red_ms": 1e3 * t_red,
+            "binding": ["hbm", "alu_fp32", "smem_red"][[t_hbm, t_alu, t_red].index(t_bind)],
+            "frac_of_binding": 1e3 * t_bind / fr["ms"], "alu_flops_per_launch": flops,
+            "alu_peak_tflops": FP32_TFLOPS, "smem_red_peak_gops": SMEM_RED_GOPS,
+            "note": "alu: 12w (kernel values) + w + 2w^2 (taps) flops per sample, 2.5 n^2 log2 n^2 + 4P^2 per cell"}
     # the whole step against the batch roofline max(bytes / HBM, method flops / tensor peak)
     tc_flops = 8.0 * P * P * sum(int(c) for c in wl.counts()[wl.counts() <= wl.tc_max_points].tolist()) \
         if wl.tc_max_points > 0 else 0.0
@@ -679,6 +702,17 @@ def run_error_vs_width(args):
           flush=True)
 
 
+def run_peaks(args):
+    """The GPU's measured compute peaks (enufft_probe_peaks) and the copy/bf16 peaks of the peaks
+    file, as one JSON line."""
+    import paper_2606_21278_b300 as enufft
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        pk = enufft.probe_peaks()
+    print(json.dumps({"peaks": pk, "hbm_gbs": _peaks()[0], "bf16_tflops": _bf16_peak()[0],
+                      "gpu": torch.cuda.get_device_name(), "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,8 +742,11 @@ def main():
                     help="local frame of every cell: centroid-aligned (default) or edge-aligned")
     ap.add_argument("--error-vs-width", action="store_true",
                     help="print the rel-l2 error against the oracle for kernel widths 4..13 (single triangle) and exit")
+    ap.add_argument("--peaks", action="store_true", help="measure the GPU's compute peaks and exit")
     args = ap.parse_args()
-    if args.error_vs_width:
+    if args.peaks:
+        run_peaks(args)
+    elif args.error_vs_width:
         run_error_vs_width(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -340,6 +340,28 @@ enufft_status enufft_get_tuning(enufft_plan plan, enufft_tuning *out);
 enufft_status enufft_tune_cache_lookup(const char *path, const char *key, enufft_tuning *out);
 enufft_status enufft_tune_cache_store(const char *path, const char *key, const enufft_tuning *t);
 
+/*
+ * Compute peaks of the current GPU for the roofline terms (the paper has no counterpart; a
+ * measurement aid).  Each figure is one launch of fixed work on every SM, timed with CUDA events on
+ * cuda_stream (best of three after a warm-up):
+ *   fp32_tflops               binary32 FMA, 8 independent chains per thread, 2 blocks of 512 per SM
+ *   f16_tflops                tcgen05.mma kind::f16 (binary16 operands in shared memory, binary32
+ *                             accumulator in tensor memory), 128 x 256 x 16 per instruction, one
+ *                             issuing thread per SM, dense flops 2 M N K per instruction
+ *   smem_red_u32_gops         shared-memory 32-bit integer reductions, every lane in its own bank
+ *   smem_red_u32_random_gops  the same at random words (bank conflicts as they fall)
+ *   smem_red_f32_gops         shared-memory binary32 add reductions, every lane in its own bank
+ * (reductions per second over the whole GPU, in units of 1e9).  Allocates and frees two small
+ * buffers; synchronises the stream.  ENUFFT_ERR_TIMEOUT if a tensor-core block's bounded wait
+ * expired.
+ */
+typedef struct {
+    double fp32_tflops, f16_tflops;
+    double smem_red_u32_gops, smem_red_u32_random_gops, smem_red_f32_gops;
+    int num_sms;
+} enufft_peaks;
+enufft_status enufft_probe_peaks(enufft_peaks *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import torch
 
 __all__ = ["Plan", "EMSParams", "EMSRetainedPower", "load_library", "LIB_PATH", "EnufftError", "tune_cache_lookup",
-           "tune_cache_store"]
+           "tune_cache_store", "probe_peaks"]
 
 LIB_PATH = os.environ.get("ENUFFT_LIB", os.path.join(os.path.dirname(os.path.abspath(__file__)), "libenufft.so"))
 _lib = None
@@ -324,6 +324,24 @@ class EMSRetainedPower(torch.autograd.Function):
         g = plan.ems_backward(coeffs, ks, sel, grad_power, ctx.params, ctx.mw)
         gh, gw = plan.type1_backward(g, x, y, h.detach(), w.detach(), ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         return gh, gw, None, None, None, None, None
+
+
+class _Peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", ctypes.c_double), ("f16_tflops", ctypes.c_double),
+                ("smem_red_u32_gops", ctypes.c_double), ("smem_red_u32_random_gops", ctypes.c_double),
+                ("smem_red_f32_gops", ctypes.c_double), ("num_sms", ctypes.c_int)]
+
+
+def probe_peaks() -> dict:
+    """Compute peaks of the current GPU (see enufft_probe_peaks), on the current stream."""
+    lib = load_library()
+    lib.enufft_probe_peaks.argtypes = [ctypes.POINTER(_Peaks), ctypes.c_void_p]
+    lib.enufft_probe_peaks.restype = ctypes.c_int
+    p = _Peaks()
+    st = lib.enufft_probe_peaks(ctypes.byref(p), _stream())
+    if st != 0:
+        raise EnufftError(f"probe_peaks: status {st}: {lib.enufft_last_error(None).decode()}")
+    return {f: getattr(p, f) for f, _ in _Peaks._fields_}
 
 
 def tune_cache_lookup(path: str, key: str) -> dict | None:
