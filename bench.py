@@ -702,6 +702,67 @@ def run_error_vs_width(args):
           flush=True)
 
 
+def run_mono_sweep(args):
+    """The monochromatic sweep of Sec. 3.1 (Table mono_sweep_config) on the GPU: for every expansion
+    ratio, window mask (triangle, square, circle) and weighting (uniform, Voronoi), the type-1
+    transform of all (dy, theta, u, Q) cells (P = 16, KB kernel) and EMS at every K_max; per cell
+    the recovered peak pair's direction error (degrees, modulo 180) and amplitude error against
+    A / 2, and K* / K_max.  Prints pooled median and standard deviation per sweep value and mask.
+    The oversampling axis leaves n_f = 64 for P = 16 (the smallest fine grid), so its rows repeat."""
+    import paper_2606_21278_b300 as enufft
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    A, P = 1000.0, 16
+    rows = {mk: [] for mk in ("triangle", "square", "circle")}
+    gpu_ms = 0.0
+    for r_exp in synth.MONO_AXES["r_exp"]:
+        wl, meta = synth.mono_sweep(r_exp, amplitude=A, modes=P)
+        g = wl.to("cuda")
+        for mk, mask in (("triangle", 0), ("square", 1), ("circle", 2)):
+            plan = enufft.Plan(g.offsets, g.nverts, g.verts, modes=P, oversamp=2.0, kernel_width=7, tol=1e-6,
+                               precision="mixed", mask=mask, eta=r_exp, kernel="kb")
+            for wname in ("uniform", "voronoi"):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                w = g.w if wname == "uniform" else plan.voronoi_weights(g.x, g.y, 64)
+                c = plan.type1(g.x, g.y, g.h, w)
+                outs = [plan.ems(c, enufft.EMSParams(k_max=K)) for K in synth.MONO_AXES["k_max"]]
+                a1.record()
+                torch.cuda.synchronize()
+                gpu_ms += a0.elapsed_time(a1)
+                plan.sync_status()
+                cn = c.cpu().numpy()
+                for K, (ks, sel, _) in zip(synth.MONO_AXES["k_max"], outs):
+                    ks, sel = ks.cpu().numpy(), sel.cpu().numpy()
+                    for j in range(wl.n_cells):
+                        if ks[j] < 1:
+                            continue
+                        p = int(sel[j, 0])
+                        m, n = p % P - P // 2, p // P - P // 2
+                        tr = math.degrees(math.atan2(n, m)) % 180.0
+                        tt = math.degrees(math.atan2(meta["n"][j], meta["m"][j])) % 180.0
+                        d = abs(tr - tt)
+                        rows[mk].append(dict(dy=meta["dy"][j], theta=meta["theta"][j], u=meta["u"][j],
+                                             r_exp=r_exp, Q=meta["Q"][j], k_max=K, weights=wname,
+                                             dtheta=min(d, 180.0 - d),
+                                             dA=abs(abs(cn[j, n + P // 2, m + P // 2]) - A / 2),
+                                             budget=ks[j] / K))
+    table = {}
+    for mk, rs in rows.items():
+        t = {}
+        for ax in ("theta", "dy", "u", "r_exp", "Q", "k_max", "weights"):
+            t[ax] = {}
+            for v in sorted({r[ax] for r in rs}, key=str):
+                sub = [r for r in rs if r[ax] == v]
+                t[ax][str(v)] = {q: [float(np.median([r[q] for r in sub])), float(np.std([r[q] for r in sub]))]
+                                 for q in ("dtheta", "dA", "budget")}
+        t["all"] = {q: [float(np.median([r[q] for r in rs])), float(np.std([r[q] for r in rs]))]
+                    for q in ("dtheta", "dA", "budget")}
+        table[mk] = t
+    print(json.dumps({"mono_sweep": table, "rows_per_mask": {k: len(v) for k, v in rows.items()},
+                      "gpu_ms": gpu_ms, "modes": P, "amplitude": A, "kernel": "kb",
+                      "sigma_axis": "no effect: n_f = 64 for every sigma at P = 16"}), flush=True)
+
+
 def run_peaks(args):
     """The GPU's measured compute peaks (enufft_probe_peaks) and the copy/bf16 peaks of the peaks
     file, as one JSON line."""
@@ -743,9 +804,12 @@ def main():
     ap.add_argument("--error-vs-width", action="store_true",
                     help="print the rel-l2 error against the oracle for kernel widths 4..13 (single triangle) and exit")
     ap.add_argument("--peaks", action="store_true", help="measure the GPU's compute peaks and exit")
+    ap.add_argument("--mono-sweep", action="store_true", help="run the monochromatic sweep (Sec. 3.1) and exit")
     args = ap.parse_args()
     if args.peaks:
         run_peaks(args)
+    elif args.mono_sweep:
+        run_mono_sweep(args)
     elif args.error_vs_width:
         run_error_vs_width(args)
     elif args.impl == "reference":

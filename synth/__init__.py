@@ -27,9 +27,10 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
-__all__ = ["Workload", "CONFIGS", "make", "plane_wave_cell", "regular_grid_square_cell"]
+__all__ = ["Workload", "CONFIGS", "make", "plane_wave_cell", "regular_grid_square_cell", "MONO_AXES", "mono_sweep"]
 
 
 @dataclass
@@ -447,3 +448,89 @@ def plane_wave_cell(q: int, amp: float, m: int, n: int, phase: float, gen: torch
                     x=(xp - half).to(dtype), y=(yp - half).to(dtype), h=h.to(dtype),
                     w=torch.full((q,), L * L / q, dtype=dtype), modes=modes, eta=1.0, mask=1,
                     precision="fp64", width=12, tol=1e-12)
+
+
+# --------------------------------------------------------------------------------------
+# monochromatic sweep (Sec. 3.1, Table mono_sweep_config)
+# --------------------------------------------------------------------------------------
+
+MONO_AXES = dict(dy=(-0.211, -0.077, 0.0), theta=(0.0, 60.0, 120.0, 180.0, 240.0, 300.0), u=(0.0, 0.5, 1.0),
+                 r_exp=(1.0, 1.5, 2.0), Q=(500, 1000, 2000), sigma=(1.25, 1.5, 2.0), k_max=(4, 6, 8, 10))
+
+
+def mono_sweep(r_exp: float, seed: int = 0, amplitude: float = 1000.0, modes: int = 16) -> tuple[Workload, dict]:
+    """One cell per (dy, theta, u, Q) of the monochromatic sweep at expansion ratio r_exp.
+
+    A cell is a triangle of base 1 and height (1 + u)/2 * sqrt(3)/2 (u = 1 equilateral), rotated by
+    theta about its centroid (the origin of its coordinates).  Its window is the square of side
+    L = 2H, H = (r_exp/2) * max extent; the sample domain D is that square moved by dy * L
+    vertically (the triangle sits dy * L above the domain's centre), with Q samples uniform on D.
+    D is split into four regions -- the triangle and the three sectors cut by the rays from the
+    centroid through the vertices -- each carrying one monochromatic elevation
+    A cos(2 pi (m x' + n y') / L + phi) with x' = x + H, y' = y + H, integer (m, n) drawn per region
+    (the triangle's mode different from its neighbours' and their negatives) and a random phase.
+    Weights are uniform, |D| / Q.  Returns the workload (cell mask, eta = r_exp) and per-cell
+    metadata: dy, theta, u, Q and the triangle's mode (m_T, n_T)."""
+    gen = torch.Generator()
+    gen.manual_seed(424242 + int(1000 * r_exp) + seed)
+    verts, xs, ys, hs, ws, counts = [], [], [], [], [], []
+    meta = {k: [] for k in ("dy", "theta", "u", "Q", "m", "n")}
+    for dy in MONO_AXES["dy"]:
+        for th in MONO_AXES["theta"]:
+            for u in MONO_AXES["u"]:
+                for Q in MONO_AXES["Q"]:
+                    hgt = 0.5 * (1.0 + u) * math.sqrt(3.0) / 2.0
+                    tri = torch.tensor([[-0.5, -hgt / 3], [0.5, -hgt / 3], [0.0, 2 * hgt / 3]], dtype=torch.float64)
+                    a = math.radians(th)
+                    rot = torch.tensor([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]], dtype=torch.float64)
+                    tri = tri @ rot.T
+                    ext = max(float(tri[:, 0].max() - tri[:, 0].min()), float(tri[:, 1].max() - tri[:, 1].min()))
+                    H = 0.5 * r_exp * ext
+                    L = 2 * H
+                    pts = (torch.rand(Q, 2, generator=gen, dtype=torch.float64) - 0.5) * L
+                    pts[:, 1] -= dy * L
+                    # regions: 0 the triangle, 1..3 the sectors between consecutive vertex rays
+                    inside = torch.ones(Q, dtype=torch.bool)
+                    for i in range(3):
+                        p0, p1 = tri[i], tri[(i + 1) % 3]
+                        cr = (p1[0] - p0[0]) * (pts[:, 1] - p0[1]) - (p1[1] - p0[1]) * (pts[:, 0] - p0[0])
+                        inside &= cr >= 0
+                    va = torch.atan2(tri[:, 1], tri[:, 0])
+                    order = torch.argsort(va)
+                    pa = torch.atan2(pts[:, 1], pts[:, 0])
+                    sector = torch.zeros(Q, dtype=torch.long)
+                    for k in range(3):
+                        lo, hi = va[order[k]], va[order[(k + 1) % 3]]
+                        sel = ((pa >= lo) & (pa < hi)) if k < 2 else ((pa >= lo) | (pa < hi))
+                        sector[sel] = k + 1
+                    region = torch.where(inside, torch.zeros_like(sector), sector)
+                    # one mode per region; the triangle's differs from the others and their negatives
+                    mt = int(torch.randint(1, 5, (1,), generator=gen))
+                    nt = int(torch.randint(-4, 5, (1,), generator=gen))
+                    mods = [(mt, nt)]
+                    while len(mods) < 4:
+                        mm = int(torch.randint(-4, 5, (1,), generator=gen))
+                        nn = int(torch.randint(-4, 5, (1,), generator=gen))
+                        if (mm, nn) not in ((0, 0), (mt, nt), (-mt, -nt)):
+                            mods.append((mm, nn))
+                    phase = torch.rand(4, generator=gen, dtype=torch.float64) * 2 * math.pi
+                    km = torch.tensor([mm for mm, _ in mods], dtype=torch.float64)[region]
+                    kn = torch.tensor([nn for _, nn in mods], dtype=torch.float64)[region]
+                    xp, yp = pts[:, 0] + H, pts[:, 1] + H
+                    h = amplitude * torch.cos(2 * math.pi * (km * xp + kn * yp) / L + phase[region])
+                    vv = torch.zeros(6, 2, dtype=torch.float64)
+                    vv[:3] = tri
+                    verts.append(vv)
+                    xs.append(pts[:, 0]); ys.append(pts[:, 1]); hs.append(h)
+                    ws.append(torch.full((Q,), L * L / Q, dtype=torch.float64))
+                    counts.append(Q)
+                    for k, v in (("dy", dy), ("theta", th), ("u", u), ("Q", Q), ("m", mt), ("n", nt)):
+                        meta[k].append(v)
+    n = len(counts)
+    off = torch.zeros(n + 1, dtype=torch.int64)
+    off[1:] = torch.cumsum(torch.tensor(counts), 0)
+    wl = Workload(name=f"mono_rexp{r_exp}", n_cells=n, nverts=torch.full((n,), 3, dtype=torch.int32),
+                  verts=torch.stack(verts), offsets=off, x=torch.cat(xs).float(), y=torch.cat(ys).float(),
+                  h=torch.cat(hs).float(), w=torch.cat(ws).float(), modes=modes, sigma=2.0, width=7, tol=1e-6,
+                  precision="mixed", eta=r_exp, mask=0)
+    return wl, {k: np.asarray(v) for k, v in meta.items()}
