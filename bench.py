@@ -345,14 +345,18 @@ def run_ours(args):
     def step(x, y, h, w):
         plan.type1_ems(x, y, h, w, prm, coeffs=coeffs, out=(ks, sel, ret))
 
-    # the step (every kernel of enufft_type1_ems) captured once in a CUDA graph and replayed
+    # the step (every kernel of enufft_type1_ems) through the plan's own CUDA graph: captured by the
+    # first call, replayed by every later one
     for _ in range(args.warmup):
         step(wl.x, wl.y, wl.h, wl.w)
     torch.cuda.synchronize()
     plan.sync_status()
-    graph = _capture(lambda: step(wl.x, wl.y, wl.h, wl.w))
+
+    def graph_step():
+        plan.type1_ems_graph(wl.x, wl.y, wl.h, wl.w, coeffs, (ks, sel, ret), prm)
+
     for _ in range(args.warmup):
-        graph.replay()
+        graph_step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     _barrier(ws)
@@ -363,7 +367,7 @@ def run_ours(args):
         t0.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
-            graph.replay()
+            graph_step()
             ev[i][1].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
@@ -478,7 +482,7 @@ def run_ours(args):
     parity = None
     if rank == 0 and not args.no_check:
         import oracle
-        graph.replay()
+        graph_step()
         torch.cuda.synchronize()
         cnt = wl.counts().cpu()
         order = torch.argsort(cnt, descending=True).tolist()
@@ -656,7 +660,7 @@ def run_ours(args):
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
                            "kernel": args.kernel, "frame": args.frame, "precision": "mixed",
                            "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
-                           "timing": "one CUDA-graph replay of enufft_type1_ems per step",
+                           "timing": "one replay per step of the plan-owned CUDA graph of enufft_type1_ems (enufft_type1_ems_graph)",
                            "l2": f"inputs larger than L2 ({16 * wl.n_points / 1e9:.2f} GB of samples per step)",
                            "parallelism": (f"cells of {ws} seeded replicas split over {ws} ranks by LPT"
                                            if ws > 1 else "1 rank")},

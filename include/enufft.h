@@ -109,6 +109,10 @@ typedef struct {
     const char *tune_cache;   /* NULL, or a JSON file of earlier tunings (read, and written on a
                                  miss) keyed by GPU name, SM count, P, n_f, w, precision, kernel,
                                  frame and tc_max_points                                        */
+    int deterministic;    /* 1 (default) or 0.  Every route is bit-reproducible run to run (the
+                             spreading sums are integer, every other reduction has a fixed
+                             order), so both values select the same code; other values return
+                             ENUFFT_ERR_ARG                                                      */
 } enufft_opts;
 
 typedef struct {
@@ -122,7 +126,7 @@ typedef struct {
 } enufft_ems_params;
 
 /* Defaults: P = 64, sigma = 2, w = 7, tol = 0, MIXED, cell mask, eta = 1.5, no tensor-core path,
- * ES kernel, centroid-aligned frame, no autotuning, no tuning cache. */
+ * ES kernel, centroid-aligned frame, no autotuning, no tuning cache, deterministic. */
 void enufft_default_opts(enufft_opts *opts);
 /* Defaults of the paper's EMS illustration (Sec. 2.2): K_min 1, K_max 12, alpha 0..0.7,
  * delta 0.02, w1 = w2 = 0.5, HEAD sums, DC excluded. */
@@ -179,6 +183,22 @@ enufft_status enufft_type1_ems(enufft_plan plan, const void *d_x, const void *d_
                                const void *d_w, void *d_coeffs, const double *d_mode_weights,
                                int mode_weights_per_cell, const enufft_ems_params *params,
                                int32_t *d_kstar, int32_t *d_sel, double *d_retained_power);
+
+/*
+ * enufft_type1_ems through a CUDA graph that the plan owns (batching of many cells into a fixed
+ * launch sequence; no counterpart in the paper, whose transforms run on a CPU).  Same arguments,
+ * results and errors as enufft_type1_ems.  The first call, and every call whose pointers, mode-
+ * weight layout or EMS parameters differ from the captured ones, captures the call's kernels on a
+ * plan-owned stream and instantiates the graph; every call then launches the graph on the plan's
+ * stream.  A replay reads the buffers named at capture: their contents may change between calls,
+ * their addresses may not without a new capture (which happens automatically).  The graph is
+ * destroyed with the plan.  Argument errors are returned before any capture; a failed capture
+ * leaves the plan without a graph and returns the error of the failing step.
+ */
+enufft_status enufft_type1_ems_graph(enufft_plan plan, const void *d_x, const void *d_y, const void *d_h,
+                                     const void *d_w, void *d_coeffs, const double *d_mode_weights,
+                                     int mode_weights_per_cell, const enufft_ems_params *params,
+                                     int32_t *d_kstar, int32_t *d_sel, double *d_retained_power);
 
 /*
  * Gradient of the EMS-retained power with the selection held fixed:
@@ -288,6 +308,8 @@ enufft_status enufft_selftest_wait_timeout(enufft_plan plan, unsigned polls);
  * placed at its cell centroid (ENUFFT_ERR_DEVICE for these; the message names each), or an
  * exhausted bounded wait (ENUFFT_ERR_TIMEOUT). */
 enufft_status enufft_sync_status(enufft_plan plan);
+/* The same call under the name of the plan it reports on. */
+enufft_status enufft_plan_sync_status(enufft_plan plan);
 
 /* Human-readable text of the last error on this plan (plan == NULL: of the calling thread). */
 const char *enufft_last_error(enufft_plan plan);

@@ -33,7 +33,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("oversamp", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("tol", ctypes.c_double), ("prec", ctypes.c_int), ("mask", ctypes.c_int),
                 ("eta", ctypes.c_double), ("tc_max_points", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("frame", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("frame", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("deterministic", ctypes.c_int)]
 
 
 class _Ems(ctypes.Structure):
@@ -84,9 +85,11 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_type1.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.enufft_ems.argtypes = [vp, vp, vp, i32, P(_Ems), vp, vp, vp]
     lib.enufft_type1_ems.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, P(_Ems), vp, vp, vp]
+    lib.enufft_type1_ems_graph.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, P(_Ems), vp, vp, vp]
     lib.enufft_ems_backward.argtypes = [vp, vp, vp, i32, P(_Ems), vp, vp, vp, vp]
     lib.enufft_type1_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.enufft_sync_status.argtypes = [vp]
+    lib.enufft_plan_sync_status.argtypes = [vp]
     lib.enufft_set_stream.argtypes = [vp, vp]
     lib.enufft_last_error.argtypes = [vp]
     lib.enufft_last_error.restype = ctypes.c_char_p
@@ -98,7 +101,8 @@ def load_library(path: str = LIB_PATH):
     lib.enufft_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P(_Tuning)]
     lib.enufft_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P(_Tuning)]
     for f in ("enufft_plan_create", "enufft_plan_destroy", "enufft_type1", "enufft_ems", "enufft_type1_ems",
-              "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status", "enufft_set_stream",
+              "enufft_type1_ems_graph", "enufft_ems_backward", "enufft_type1_backward", "enufft_sync_status",
+              "enufft_plan_sync_status", "enufft_set_stream",
               "enufft_get_plan_info", "enufft_selftest_wait_timeout", "enufft_reconstruct",
               "enufft_voronoi_weights", "enufft_get_tuning", "enufft_tune_cache_lookup", "enufft_tune_cache_store"):
         getattr(lib, f).restype = ctypes.c_int
@@ -138,7 +142,8 @@ class Plan:
     def __init__(self, offsets: torch.Tensor, nverts: torch.Tensor, verts: torch.Tensor, modes: int = 64,
                  oversamp: float = 2.0, kernel_width: int = 7, tol: float = 0.0, precision: str = "mixed",
                  mask: str | int = "cell", eta: float = 1.5, tc_max_points: int = 0, kernel: str = "es",
-                 frame: str | int = "centroid", autotune: bool = False, tune_cache: str | None = None):
+                 frame: str | int = "centroid", autotune: bool = False, tune_cache: str | None = None,
+                 deterministic: bool = True):
         self._lib = load_library()
         if not torch.cuda.is_available():
             raise EnufftError("no CUDA device")
@@ -158,7 +163,7 @@ class Plan:
         o = _Opts(modes, oversamp, kernel_width, tol, _PREC[precision],
                   _MASK[mask] if isinstance(mask, str) else int(mask), eta, tc_max_points, _KERNEL[kernel],
                   _FRAME[frame] if isinstance(frame, str) else int(frame), int(bool(autotune)),
-                  tune_cache.encode() if tune_cache else None)
+                  tune_cache.encode() if tune_cache else None, int(bool(deterministic)))
         h = ctypes.c_void_p()
         st = self._lib.enufft_plan_create(ctypes.byref(h), ctypes.byref(o), self.n_cells, _ptr(self.offsets),
                                           _ptr(self.nverts), _ptr(self.verts), _stream())
@@ -280,6 +285,21 @@ class Plan:
         self._bind()
         self._check(self._lib.enufft_type1_ems(self._h, _ptr(x), _ptr(y), _ptr(h), _ptr(w), _ptr(coeffs), _ptr(mw),
                                                per, ctypes.byref(pc), _ptr(ks), _ptr(sel), _ptr(ret)), "type1_ems")
+        return coeffs, ks, sel, ret
+
+    def type1_ems_graph(self, x, y, h, w, coeffs, out, params: EMSParams = EMSParams(), mode_weights=None):
+        """type1_ems through the plan's own CUDA graph (enufft_type1_ems_graph): captured on the first
+        call and again whenever a buffer or parameter changes, replayed otherwise.  `coeffs` and
+        `out` = (kstar, sel, retained) must stay allocated while the graph may replay."""
+        x, y, h, w = self._samples(x, y, h, w)
+        ks, sel, ret = out
+        mw, per = self._weights(mode_weights)
+        self._graph_keep = (x, y, h, w, coeffs, ks, sel, ret, mw)   # buffers the graph reads or writes
+        pc = params.c()
+        self._bind()
+        self._check(self._lib.enufft_type1_ems_graph(self._h, _ptr(x), _ptr(y), _ptr(h), _ptr(w), _ptr(coeffs),
+                                                     _ptr(mw), per, ctypes.byref(pc), _ptr(ks), _ptr(sel),
+                                                     _ptr(ret)), "type1_ems_graph")
         return coeffs, ks, sel, ret
 
     def ems_backward(self, coeffs, kstar, sel, grad_power, params: EMSParams = EMSParams(), mode_weights=None):

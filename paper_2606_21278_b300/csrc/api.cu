@@ -122,6 +122,19 @@ struct enufft_plan_s {
     std::vector<int64_t> h_off;
     float* d_pgrid = nullptr;
     void* d_pbuf = nullptr;
+    // plan-owned CUDA graph of enufft_type1_ems and the arguments it was captured with
+    struct GraphKey {
+        const void *x, *y, *h, *w;
+        void* coeffs;
+        const double* mw;
+        int per_cell;
+        enufft_ems_params prm;
+        int32_t *kstar, *sel;
+        double* ret;
+    };
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    GraphKey gkey = {};
     std::string err;
 };
 
@@ -278,6 +291,7 @@ void enufft_default_opts(enufft_opts* o) {
     o->frame = ENUFFT_FRAME_CENTROID;
     o->autotune = 0;
     o->tune_cache = nullptr;
+    o->deterministic = 1;
 }
 
 void enufft_default_ems(enufft_ems_params* p) {
@@ -323,6 +337,8 @@ enufft_status enufft_plan_destroy(enufft_plan p) {
     cudaFree(p->d_rot);
     cudaFree(p->d_vx);
     cudaFree(p->d_vy);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
     cudaSetDevice(cur);
     delete p;
     return ENUFFT_OK;
@@ -356,6 +372,8 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     if (o.frame != ENUFFT_FRAME_CENTROID && o.frame != ENUFFT_FRAME_EDGE)
         return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: bad frame");
     if (o.autotune != 0 && o.autotune != 1) return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: autotune must be 0 or 1");
+    if (o.deterministic != 0 && o.deterministic != 1)
+        return fail(nullptr, ENUFFT_ERR_ARG, "plan_create: deterministic must be 0 or 1");
 
     enufft_plan p = new enufft_plan_s();
     p->opts = o;
@@ -734,6 +752,8 @@ enufft_status enufft_sync_status(enufft_plan p) {
     return ENUFFT_OK;
 }
 
+enufft_status enufft_plan_sync_status(enufft_plan p) { return enufft_sync_status(p); }
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------------
@@ -976,6 +996,68 @@ enufft_status enufft_type1_ems(enufft_plan p, const void* d_x, const void* d_y, 
     const EmsArgs ea = make_ems(prm, d_mode_weights, per_cell, d_kstar, d_sel, d_retained);
     return p->dbl ? run_type1<double>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea)
                   : run_type1<float>(p, d_x, d_y, d_h, d_w, d_coeffs, &ea);
+}
+
+static bool same_key(const enufft_plan_s::GraphKey& a, const enufft_plan_s::GraphKey& b) {
+    return a.x == b.x && a.y == b.y && a.h == b.h && a.w == b.w && a.coeffs == b.coeffs && a.mw == b.mw &&
+           a.per_cell == b.per_cell && a.kstar == b.kstar && a.sel == b.sel && a.ret == b.ret &&
+           a.prm.k_min == b.prm.k_min && a.prm.k_max == b.prm.k_max && a.prm.alpha_min == b.prm.alpha_min &&
+           a.prm.alpha_max == b.prm.alpha_max && a.prm.delta == b.prm.delta && a.prm.w1 == b.prm.w1 &&
+           a.prm.w2 == b.prm.w2 && a.prm.sum_over == b.prm.sum_over && a.prm.include_dc == b.prm.include_dc;
+}
+
+enufft_status enufft_type1_ems_graph(enufft_plan p, const void* d_x, const void* d_y, const void* d_h,
+                                     const void* d_w, void* d_coeffs, const double* d_mode_weights, int per_cell,
+                                     const enufft_ems_params* prm, int32_t* d_kstar, int32_t* d_sel,
+                                     double* d_retained) {
+    if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "type1_ems_graph: NULL plan");
+    enufft_status st = check_ems_params(p, prm);
+    if (st != ENUFFT_OK) return st;
+    if (p->n_cells == 0) return ENUFFT_OK;
+    if (!d_coeffs || !d_kstar || !d_sel || !d_retained || (p->n_points > 0 && (!d_x || !d_y || !d_h || !d_w)))
+        return fail(p, ENUFFT_ERR_ARG, "type1_ems_graph: NULL data pointer");
+    if (!aligned16(d_coeffs)) return fail(p, ENUFFT_ERR_ARG, "type1_ems_graph: coeffs must be 16-byte aligned");
+    cudaSetDevice(p->device);
+    const enufft_plan_s::GraphKey key = {d_x, d_y, d_h, d_w, d_coeffs, d_mode_weights, per_cell, *prm,
+                                         d_kstar, d_sel, d_retained};
+    if (!p->gexec || !same_key(key, p->gkey)) {
+        if (p->gexec) {
+            cudaError_t e = cudaStreamSynchronize(p->stream);   // the old graph may still run
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+            if (e != cudaSuccess) return cuda_fail(p, e, "type1_ems_graph: synchronise");
+        }
+        cudaError_t e = cudaSuccess;
+        if (!p->gstream) e = cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(p, e, "type1_ems_graph: stream");
+        // capture on the plan's own stream (the caller's may be the legacy default stream, which
+        // cannot be captured); the kernels are recorded, not run
+        const cudaStream_t user = p->stream;
+        p->stream = p->gstream;
+        e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            p->stream = user;
+            return cuda_fail(p, e, "type1_ems_graph: begin capture");
+        }
+        st = enufft_type1_ems(p, d_x, d_y, d_h, d_w, d_coeffs, d_mode_weights, per_cell, prm, d_kstar, d_sel,
+                              d_retained);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->gstream, &graph);
+        p->stream = user;
+        if (st != ENUFFT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return cuda_fail(p, e, "type1_ems_graph: capture");
+        }
+        p->gkey = key;
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, p->stream);
+    return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "type1_ems_graph: launch");
 }
 
 enufft_status enufft_ems(enufft_plan p, const void* d_coeffs, const double* d_mode_weights, int per_cell,

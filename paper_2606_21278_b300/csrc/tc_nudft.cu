@@ -17,11 +17,12 @@
 // is therefore limited to 256 samples (two banks of 128 TMEM columns alternate), and finished runs
 // are added into the staged spectrum in shared memory with round-to-nearest binary32 additions.
 //
-// One CTA per cell at a time (two per SM), warp-specialised: a control warp sets up the samples of
-// the chunk two ahead (window, scaled weight, coordinates, unit phasor steps) and issues the tcgen05
-// MMAs; eight operand warps turn each chunk of 32 samples into binary16 operands in shared memory
-// (double buffered).  The hand-offs are mbarriers with bounded waits (set-up ready, operands
-// written, MMAs done), so the operand warps never wait on a block-wide barrier inside a cell.  The
+// One CTA per cell at a time (two per SM), warp-specialised: two set-up warps, one per stage, each
+// prepare every other chunk of samples (window, scaled weight, coordinates, unit phasor steps) with
+// the samples of their next chunk already loaded; one warp issues the tcgen05 MMAs; eight operand
+// warps turn each chunk of 32 samples into binary16 operands in shared memory (double buffered).
+// The hand-offs are mbarriers with bounded waits (set-up ready, operands written, MMAs done), so
+// the operand warps never wait on a block-wide barrier inside a cell.  The
 // accumulator lives in tensor memory and is read back per run, combined through shared memory,
 // written out and ranked for EMS (Sec. 2.2).
 #include <cuda_fp16.h>
@@ -36,8 +37,9 @@ namespace enufft {
 namespace {
 
 constexpr int kFeatThreads = 256;                         // warps 0..7: operands, TMEM read-back
-constexpr int kTcThreads = kFeatThreads + 32;             // warp 8: sample set-up and MMA issue
-constexpr int kCtlWarp = kFeatThreads / 32;
+constexpr int kMmaWarp = kFeatThreads / 32;               // warp 8: MMA issue
+constexpr int kPrepWarp0 = kMmaWarp + 1;                  // warps 9, 10: sample set-up of stage 0, 1
+constexpr int kTcThreads = kFeatThreads + 3 * 32;
 constexpr int kCh = 32;                                   // samples per chunk (K of one stage)
 constexpr unsigned kOpBytes = kCh * tc::kTcFeat * 2;      // one operand (8 KB)
 constexpr unsigned kStageBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
@@ -240,6 +242,21 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
         const CellConst& cc = a.cells[cell];
         const int64_t q0 = a.offsets[cell], q1 = a.offsets[cell + 1];
         const bool valid = cc.valid != 0;
+        // ---- the samples toward L2 ahead of use: this cell's coordinates when it is the CTA's first,
+        // the next cell's four arrays always (the control warp's one-chunk lookahead then waits on
+        // L2, not on DRAM)
+        if (li == (int)blockIdx.x) {
+            prefetch_l2(a.x, q0, q1, tid, kTcThreads);
+            prefetch_l2(a.y, q0, q1, tid, kTcThreads);
+        }
+        if (li + (int)gridDim.x < a.n_list) {
+            const int nc = a.list[li + gridDim.x];
+            const int64_t n0 = a.offsets[nc], n1 = a.offsets[nc + 1];
+            prefetch_l2(a.x, n0, n1, tid, kTcThreads);
+            prefetch_l2(a.y, n0, n1, tid, kTcThreads);
+            prefetch_l2(a.h, n0, n1, tid, kTcThreads);
+            prefetch_l2(a.w, n0, n1, tid, kTcThreads);
+        }
         // ---- scale: max |w h| / |D| over the cell (binary32)
         float cm = 0.0f;
         if (valid)
@@ -256,33 +273,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
         const float inv_cm = cm > 0.0f ? 1.0f / cm : 0.0f;
         const int nch = (valid && cm > 0.0f) ? (int)((q1 - q0 + kCh - 1) / kCh) : 0;
 
-        if (warp == kCtlWarp) {
-            // ---- control warp: set-up two chunks ahead (loads one further ahead), MMA issue
-            const FastFrame ff = fast_frame(cc);
-            const float inv_nf = 1.0f / (float)a.NF;
-            float rx = 0.f, ry = 0.f, rh = 0.f, rw = 0.f;
-            bool rv = false;
-            auto load = [&](int ch) {
-                const int64_t q = q0 + (int64_t)ch * kCh + lane;
-                rv = ch < nch && q < q1;
-                if (rv) {
-                    rx = a.x[q];
-                    ry = a.y[q];
-                    rh = a.h[q];
-                    rw = a.w[q];
-                }
-            };
-            auto setup = [&](int ch) {   // set-up of chunk ch from the loaded samples, then signal
-                const unsigned st = (g + ch) & 1u;
-                tc_prep_sample(ff, cc, rv, rx, ry, rh, rw, inv_cm, inv_nf, prep + st * kPrepF * kCh, lane, a.status);
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_prep[st]));
-            };
-            for (int ch = 0; ch < 2 && ch < nch; ++ch) {
-                load(ch);
-                setup(ch);
-            }
-            if (nch > 2) load(2);
+        if (warp == kMmaWarp) {
+            // ---- MMA warp: the three split products of each chunk once its operands are written
             for (int ch = 0; ch < nch; ++ch) {
                 const unsigned gc = g + ch, st = gc & 1u;
                 if (!tc::mbar_wait(tc::smem_addr(&bar_full[st]), (gc >> 1) & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
@@ -304,10 +296,35 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
                     tc::mma_commit(tc::smem_addr(&bar_mma[st]));
                 }
                 __syncwarp();
-                if (ch + 2 < nch) {
-                    setup(ch + 2);   // this stage's set-up buffer was read by chunk ch, whose operands are written
-                    if (ch + 3 < nch) load(ch + 3);
+            }
+        } else if (warp >= kPrepWarp0) {
+            // ---- set-up warp of stage sp: chunks ch with (g + ch) & 1 == sp, each into the stage's
+            // set-up buffer once the operand warps have written the chunk two before (which read it)
+            const unsigned sp = (unsigned)(warp - kPrepWarp0);
+            const FastFrame ff = fast_frame(cc);
+            const float inv_nf = 1.0f / (float)a.NF;
+            float rx = 0.f, ry = 0.f, rh = 0.f, rw = 0.f;
+            bool rv = false;
+            auto load = [&](int ch) {
+                const int64_t q = q0 + (int64_t)ch * kCh + lane;
+                rv = ch < nch && q < q1;
+                if (rv) {
+                    rx = a.x[q];
+                    ry = a.y[q];
+                    rh = a.h[q];
+                    rw = a.w[q];
                 }
+            };
+            const int c0 = (int)((sp - g) & 1u);
+            if (c0 < nch) load(c0);
+            for (int ch = c0; ch < nch; ch += 2) {
+                const unsigned gc = g + ch;
+                if (ch >= 2 && !tc::mbar_wait(tc::smem_addr(&bar_full[sp]), ((gc - 2) >> 1) & 1u, kWaitLimit))
+                    atomicOr(a.status, ST_TIMEOUT);
+                tc_prep_sample(ff, cc, rv, rx, ry, rh, rw, inv_cm, inv_nf, prep + sp * kPrepF * kCh, lane, a.status);
+                if (ch + 2 < nch) load(ch + 2);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_prep[sp]));
             }
         } else {
             // ---- operand warps

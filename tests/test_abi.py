@@ -51,7 +51,7 @@ def test_defaults(lib):
     o = enufft._Opts()
     lib.enufft_default_opts(ctypes.byref(o))
     assert (o.modes, o.oversamp, o.kernel_width, o.prec, o.mask, o.eta, o.tc_max_points, o.kernel, o.frame,
-            o.autotune, o.tune_cache) == (64, 2.0, 7, 2, 0, 1.5, 0, 0, 0, 0, None)
+            o.autotune, o.tune_cache, o.deterministic) == (64, 2.0, 7, 2, 0, 1.5, 0, 0, 0, 0, None, 1)
     e = enufft._Ems()
     lib.enufft_default_ems(ctypes.byref(e))
     assert (e.k_min, e.k_max, e.alpha_min, e.alpha_max, e.delta, e.w1, e.w2, e.sum_over, e.include_dc) == \
@@ -61,7 +61,8 @@ def test_defaults(lib):
 @pytest.mark.parametrize("field,value", [("modes", 7), ("modes", 0), ("modes", 256), ("oversamp", 1.5),
                                          ("kernel_width", 1), ("kernel_width", 17), ("prec", 9), ("mask", 5),
                                          ("eta", 0.0), ("tol", -1.0), ("tc_max_points", -1), ("kernel", 2),
-                                         ("kernel", -1), ("frame", 2), ("frame", -1)])
+                                         ("kernel", -1), ("frame", 2), ("frame", -1), ("autotune", 2),
+                                         ("deterministic", 2), ("deterministic", -1)])
 def test_plan_create_rejects_bad_options(lib, field, value):
     o = enufft._Opts()
     lib.enufft_default_opts(ctypes.byref(o))
