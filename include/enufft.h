@@ -299,7 +299,8 @@ enufft_status enufft_ems_noalloc(int modes, int64_t n_cells, const void *d_coeff
  * giving up after `polls` polls exactly as the tensor-core kernel does when a hand-off never
  * comes: the block latches the timeout bit in the plan's status word and returns, so the context
  * stays usable.  The next enufft_sync_status then returns ENUFFT_ERR_TIMEOUT ("bounded wait
- * expired").  polls must be in [1, 2^20]; a NULL plan or a bad count returns ENUFFT_ERR_ARG.
+ * expired").  Each poll suspends the waiting warp for at most about 20 us, so the wait ends within
+ * about polls * 20 us.  polls must be in [1, 2^17]; a NULL plan or a bad count returns ENUFFT_ERR_ARG.
  */
 enufft_status enufft_selftest_wait_timeout(enufft_plan plan, unsigned polls);
 

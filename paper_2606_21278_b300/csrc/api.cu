@@ -727,7 +727,7 @@ enufft_status enufft_set_stream(enufft_plan p, void* s) {
 
 enufft_status enufft_selftest_wait_timeout(enufft_plan p, unsigned polls) {
     if (!p) return fail(nullptr, ENUFFT_ERR_ARG, "selftest_wait_timeout: NULL plan");
-    if (polls < 1 || polls > (1u << 20)) return fail(p, ENUFFT_ERR_ARG, "selftest_wait_timeout: polls must be in [1, 2^20]");
+    if (polls < 1 || polls > (1u << 17)) return fail(p, ENUFFT_ERR_ARG, "selftest_wait_timeout: polls must be in [1, 2^17]");
     cudaSetDevice(p->device);
     cudaError_t e = launch_wait_timeout(polls, p->d_ctr + 2, p->stream);
     return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "selftest_wait_timeout: launch");

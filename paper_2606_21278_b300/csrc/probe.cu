@@ -18,7 +18,7 @@ constexpr int kProbeThreads = 512;
 constexpr int kFmaIters = 4096;
 constexpr int kRedIters = 1024;
 constexpr int kMmaIters = 4096;
-constexpr unsigned kMmaWait = 1u << 22;
+constexpr unsigned kMmaWait = 1u << 17;
 constexpr int kMmaPadSmem = 120 * 1024;   // dynamic shared memory that keeps one probe CTA per SM
 
 __global__ void __launch_bounds__(kProbeThreads, 2) probe_fma_kernel(float* sink, float seed) {

@@ -37,19 +37,22 @@ __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_arrive(unsigned addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
+// One poll: true once the phase with the given parity has completed.  A waiting thread is suspended
+// (its warp issues nothing) until the phase completes or about kPollNs nanoseconds have passed.
+constexpr unsigned kPollNs = 20000;
 __device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(addr), "r"(parity)
+        : "r"(addr), "r"(parity), "r"(kPollNs)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete, at most `limit` polls (each try_wait
-// itself suspends for a bounded, hardware-chosen time).  Returns false when the limit ran out.
+// Wait for the phase with the given parity to complete, at most `limit` polls (so at most about
+// limit * kPollNs nanoseconds).  Returns false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, unsigned limit) {
     for (unsigned i = 0; i < limit; ++i)
         if (mbar_test(addr, parity)) return true;
@@ -95,17 +98,54 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 8 consecutive 32-bit columns of the thread's lane
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8]) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+// one 32-bit column of the thread's lane
+__device__ __forceinline__ float tmem_ld1(unsigned taddr) {
+    unsigned r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return __uint_as_float(r);
+}
+// the thread's lane, 16 consecutive 32-bit columns from registers
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])),
+          "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+          "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+          "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- operand layout (MN-major, no swizzle) of one chunk of samples (the K dimension, a multiple
-// of 16) and 128 features (the M or N dimension): 8 x 8 core matrices of 128 B, the 16 feature
-// blocks of one sample octet contiguous (stride 128 B), sample octets 2048 B apart.  The MMA of K
-// step s (16 samples) starts at s * 4096 B with LBO = 2048 and SBO = 128.
-constexpr int kTcFeat = 128;
-constexpr unsigned kTcLbo = 2048, kTcSbo = 128;
-__host__ __device__ constexpr unsigned tc_off(int feature, int k) {
-    return (unsigned)((k >> 3) * 2048 + (feature >> 3) * 128 + (k & 7) * 16 + (feature & 7) * 2);
-}
+// of 16) and NFEAT features (the M or N dimension, a multiple of 16): 8 x 8 core matrices of 128 B,
+// the NFEAT / 8 feature blocks of one sample octet contiguous (stride 128 B = SBO), sample octets
+// NFEAT * 16 B apart (= LBO).  The MMA of K step s (16 samples) starts at s * NFEAT * 32 B.
+template <int NFEAT>
+struct OpLayout {
+    static_assert(NFEAT % 16 == 0, "feature count");
+    static constexpr unsigned kLbo = NFEAT * 16, kSbo = 128, kKStep = NFEAT * 32;
+    __host__ __device__ static constexpr unsigned off(int feature, int k) {
+        return (unsigned)((k >> 3) * (NFEAT * 16) + (feature >> 3) * 128 + (k & 7) * 16 + (feature & 7) * 2);
+    }
+};
 
 }  // namespace tc
 }  // namespace enufft

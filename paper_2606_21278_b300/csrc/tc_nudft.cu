@@ -3,28 +3,35 @@
 //
 //   h^[n][m] = (1/|D|) sum_q win_q w_q h_q e^{-i k_n y'_q} e^{-i k_m x'_q},   k = 2 pi / L,
 //
-// i.e. D = A^T B with A[q][.] = c_q (e^{-i k_n y'_q})_n and B[q][.] = (e^{-i k_m x'_q})_m over the
-// samples q of the cell.  Complex values are stacked as real features (rows 0..63 the real parts
-// of modes -P/2 .. P/2-1, rows 64..127 the imaginary parts), so one 128 x 128 real product per
-// 16 samples carries the whole P x P complex result (P <= 64):
-//   Re h^ = D[re n][re m] - D[im n][im m],   Im h^ = D[re n][im m] + D[im n][re m].
+// i.e. D = A^T B with A[q][.] = c_q (e^{-i k_n y'_q})_n over n in [-P/2, P/2) and
+// B[q][.] = (e^{-i k_m' x'_q})_m' over m' in [0, P/2] only: the samples are real, so the phasor of
+// -m' is the conjugate of that of m', and with P1 = D[re n][re m'], P2 = D[im n][im m'],
+// P3 = D[im n][re m'], P4 = D[re n][im m']
+//   h^[n][ m'] = (P1 - P2) + i (P3 + P4),   h^[n][-m'] = (P1 + P2) + i (P3 - P4).
+// Complex values are stacked as real features: A has 128 (the real and imaginary parts of 16
+// consecutive modes n alternate in blocks of 16, so both sit in one 32-lane quarter of the
+// accumulator), B has 80 (likewise for m' = 0..31, then the real and imaginary parts of m' = 32),
+// so one 128 x 80 real product per 16 samples carries the whole P x P complex result (P <= 64).
 // Each value is split into binary16 hi + lo and the product is accumulated in binary32 as
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo * lo term is below 2^-22 of the scale).  The samples'
 // weights are scaled by 1 / max |c| of the cell so that every operand lies in [-1, 1].
 //
 // The tensor core adds the products of every MMA to the binary32 accumulator without rounding to
 // nearest, so the accumulator error grows with the number of MMAs it absorbs; each accumulator run
-// is therefore limited to 256 samples (two banks of 128 TMEM columns alternate), and finished runs
-// are added into the staged spectrum in shared memory with round-to-nearest binary32 additions.
+// is therefore limited to 256 samples (two banks of TMEM columns alternate), and every thread adds
+// its lane's part of a finished run into a running total, also in TMEM, with round-to-nearest
+// binary32 additions (no shared memory, no block barrier).  At the end of a cell each spectrum
+// entry is formed by one operand thread, which combines the four products of its accumulator lane
+// with those of the lane 16 apart by shuffles.
 //
-// One CTA per cell at a time (two per SM), warp-specialised: two set-up warps, one per stage, each
-// prepare every other chunk of samples (window, scaled weight, coordinates, unit phasor steps) with
-// the samples of their next chunk already loaded; one warp issues the tcgen05 MMAs; eight operand
-// warps turn each chunk of 32 samples into binary16 operands in shared memory (double buffered).
-// The hand-offs are mbarriers with bounded waits (set-up ready, operands written, MMAs done), so
-// the operand warps never wait on a block-wide barrier inside a cell.  The
-// accumulator lives in tensor memory and is read back per run, combined through shared memory,
-// written out and ranked for EMS (Sec. 2.2).
+// One CTA per cell at a time (two per SM), warp-specialised: two set-up warps each prepare every
+// other chunk of samples (window, scaled weight, coordinates, unit phasor steps) into a ring of four
+// set-up buffers, with the samples of their next chunk already loaded; one warp issues the tcgen05
+// MMAs; eight operand warps turn each chunk of 32 samples into binary16 operands in shared memory
+// (four stages).  The hand-offs are mbarriers with bounded waits (set-up ready, set-up read,
+// operands written, MMAs done), so
+// the operand warps never wait on a block-wide barrier inside a cell.  The spectrum is written out
+// and ranked for EMS (Sec. 2.2).
 #include <cuda_fp16.h>
 
 #include "ems.cuh"
@@ -41,23 +48,40 @@ constexpr int kMmaWarp = kFeatThreads / 32;               // warp 8: MMA issue
 constexpr int kPrepWarp0 = kMmaWarp + 1;                  // warps 9, 10: sample set-up of stage 0, 1
 constexpr int kTcThreads = kFeatThreads + 3 * 32;
 constexpr int kCh = 32;                                   // samples per chunk (K of one stage)
-constexpr unsigned kOpBytes = kCh * tc::kTcFeat * 2;      // one operand (8 KB)
-constexpr unsigned kStageBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
+constexpr int kFeatA = 128, kFeatB = 80;                  // stacked features of A (n) and B (m' >= 0)
+using LayA = tc::OpLayout<kFeatA>;
+using LayB = tc::OpLayout<kFeatB>;
+constexpr unsigned kOpA = kCh * kFeatA * 2;               // one A operand (8 KB)
+constexpr unsigned kOpB = kCh * kFeatB * 2;               // one B operand (5 KB)
+constexpr unsigned kStageBytes = 2 * kOpA + 2 * kOpB;     // A_hi, A_lo, B_hi, B_lo
+constexpr int kStages = 4;                                // operand stages (chunk g uses g % 4)
 constexpr int kHS = 65;                                   // row stride (complex) of the staged spectrum
-constexpr unsigned kSpecOff = 2 * kStageBytes;
+// at the end of a cell the staged spectrum and the EMS scratch take the free stage memory
+constexpr unsigned kSpecOff = 0;
 constexpr unsigned kSpecBytes = 64 * kHS * 8;
-constexpr int kPrepF = 9;                                 // per sample: c, tx hi/lo, ty hi/lo, x and y steps
-constexpr unsigned kPrepOff = kSpecOff + kSpecBytes;
-constexpr unsigned kPrepBytes = 2 * kPrepF * kCh * 4;
-constexpr unsigned kEmsOff = kPrepOff + kPrepBytes;
+constexpr unsigned kEmsOff = kSpecOff + kSpecBytes;
 constexpr unsigned kEmsBytes = (unsigned)((ems_smem_bytes(kTcThreads / 32, kEmsMaxK) + 15) / 16 * 16);
-constexpr unsigned kMiscOff = kEmsOff + kEmsBytes;
-constexpr unsigned kSmemBytes = kMiscOff + 128;
-constexpr unsigned kWaitLimit = 1u << 22;
+constexpr int kPrepF = 9;                                 // per sample: c, tx hi/lo, ty hi/lo, x and y steps
+constexpr int kPrepBufs = 4;                             // ring of set-up buffers (chunk g uses g % 4)
+constexpr unsigned kPrepOff = kStages * kStageBytes;
+constexpr unsigned kPrepBytes = kPrepBufs * kPrepF * kCh * 4;
+constexpr unsigned kMiscOff = kPrepOff + kPrepBytes;
+constexpr unsigned kSmemBytes = kMiscOff + 192;
+constexpr unsigned kWaitLimit = 1u << 17;                // polls of a bounded wait (about 2.6 s)
 constexpr int kBlockChunks = 8;                           // chunks accumulated per TMEM run (256 samples)
-constexpr unsigned kTmemCols = 256;                       // two 128-column accumulator banks
-static_assert(kCh % 16 == 0 && tc::tc_off(127, kCh - 1) < kOpBytes, "operand layout");
+constexpr unsigned kTmemCols = 256;                       // run banks at columns 0 and 128, the total beside
+static_assert(kEmsOff + kEmsBytes <= kStages * kStageBytes, "spectrum and EMS scratch fit the stage memory");
+static_assert(kCh % 16 == 0 && LayA::off(kFeatA - 1, kCh - 1) < kOpA && LayB::off(kFeatB - 1, kCh - 1) < kOpB,
+              "operand layout");
+static_assert(kStageBytes % 16 == 0 && kOpA % 16 == 0 && kOpB % 16 == 0, "descriptor alignment");
 static_assert(kFeatThreads == 8 * kCh, "one (sample, feature octet) task per operand thread and axis");
+static_assert(144 + 4 * (kTcThreads / 32) <= 192, "barriers, TMEM base and warp maxima fit the misc area");
+
+// feature of the real part of the first mode of octet o (modes 8 o .. 8 o + 7 of A, or of B for
+// o < 4): blocks of 16 real parts followed by their 16 imaginary parts; the imaginary part of a
+// mode is 16 features later, except in B's last octet (m' = 32 .. 39: real 64.., imaginary 72..)
+__host__ __device__ constexpr int feat_re(int o) { return 32 * (o >> 1) + 8 * (o & 1); }
+__host__ __device__ constexpr int feat_im_b(int o) { return o == 4 ? 72 : feat_re(o) + 16; }
 
 struct TcSpec {
     const cplx<float>* hs;
@@ -84,11 +108,11 @@ struct TcArgs {
 };
 
 // c e^{-2 pi i m (t + 1/2)} for m = m0 .. m0 + 7 (t = th + tl, |t| <= 1/2; (wr, wi) = -e^{-2 pi i t}),
-// zero beyond slot P unless FULL (P = 64).  The anchor m0 takes one fast sine/cosine of an argument
+// zero from slot `lim` on unless FULL.  The anchor m0 takes one fast sine/cosine of an argument
 // reduced to [-pi, pi] (absolute error below 1e-6); the 7 rotations use the accurate step.
 template <bool FULL>
-__device__ __forceinline__ void tc_phasors(float th, float tl, float wr, float wi, float c, int m0, int slot0, int P,
-                                           float (&re)[8], float (&im)[8]) {
+__device__ __forceinline__ void tc_phasors(float th, float tl, float wr, float wi, float c, int m0, int slot0, int lim,
+                                           float (&re)[8], float (&im)[8], float& nr8, float& ni8) {
     const float fm0 = (float)m0;
     const float p = fm0 * th;
     const float r = (p - rintf(p)) + __fmaf_rn(fm0, tl, __fmaf_rn(fm0, th, -p));
@@ -98,13 +122,15 @@ __device__ __forceinline__ void tc_phasors(float th, float tl, float wr, float w
     float zr = sg * c0, zi = -sg * s0;     // c (-1)^{m0} e^{-2 pi i m0 t}
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const bool on = FULL || slot0 + j < P;
+        const bool on = FULL || slot0 + j < lim;
         re[j] = on ? zr : 0.0f;
         im[j] = on ? zi : 0.0f;
         const float nr = zr * wr - zi * wi, ni = zr * wi + zi * wr;
         zr = nr;
         zi = ni;
     }
+    nr8 = zr;   // the mode m0 + 8
+    ni8 = zi;
 }
 
 // Setup of one sample (Sec. 2.1, App. A): window test, scaled weight c / max |c|, and the centred
@@ -170,36 +196,75 @@ __device__ __forceinline__ void tc_split8(const float (&v)[8], uint4& hi, uint4&
     lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
-__device__ __forceinline__ void feat_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFeatThreads) : "memory"); }
+// TMEM column of column c (0 .. 79) of the running total: columns 80 .. 127 and 208 .. 255, beside
+// the two 80-column run banks at 0 and 128
+__device__ __forceinline__ unsigned total_col(int c) { return c < 48 ? 80u + (unsigned)c : 160u + (unsigned)c; }
 
-// hs[n][m] += (D[re n][re m] - D[im n][im m], D[re n][im m] + D[im n][re m]) for one accumulator
-// bank; taken by the 256 operand threads (TMEM lane quarter warp & 3, column half warp >> 2), in
-// two passes of 16 columns
-__device__ __forceinline__ void tc_flush(unsigned bank, cplx<float>* hs, int warp, int lane) {
-    const int lg = warp & 3, chh = warp >> 2;
-    const int row = 32 * lg + lane;
-    feat_sync();   // earlier writes of hs by other operand threads are complete
+// The thread's lane of the finished run in `bank` into the running total (the first run of a cell
+// is copied).  Warp w takes lane quarter w & 3 and the accumulator columns of its B modes:
+// 0 .. 31 (w < 4) or 32 .. 79 (w >= 4).
+__device__ __forceinline__ void tc_accumulate(unsigned tmem, unsigned bank, int warp, bool first) {
+    const unsigned lanes = (unsigned)(32 * (warp & 3)) << 16;
+    const int nseg = warp < 4 ? 4 : 6, c0 = warp < 4 ? 0 : 32;
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        const int c0 = 32 * chh + 16 * pass;
-        const unsigned ta = bank + ((unsigned)(32 * lg) << 16) + c0;
-        float vr[16], vi[16];
-        tc::tmem_ld16(ta, vr);
-        tc::tmem_ld16(ta + 64, vi);
+    for (int sg = 0; sg < nseg; ++sg) {   // 8 columns at a time
+        const int c = c0 + 8 * sg;
+        float v[8], t[8];
+        tc::tmem_ld8(tmem + lanes + bank + (unsigned)c, v);
+        if (!first) tc::tmem_ld8(tmem + lanes + total_col(c), t);
         tc::tmem_ld_wait();
-        cplx<float>* dst = hs + (row & 63) * kHS + c0;
-        if (row < 64) {
+        if (!first) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) dst[j] = cplx<float>{dst[j].re + vr[j], dst[j].im + vi[j]};
+            for (int j = 0; j < 8; ++j) v[j] = __fadd_rn(v[j], t[j]);
         }
-        feat_sync();
-        if (row >= 64) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) dst[j] = cplx<float>{dst[j].re - vi[j], dst[j].im + vr[j]};
-        }
-        feat_sync();
+        tc::tmem_st8(tmem + lanes + total_col(c), v);
     }
+    tc::tmem_st_wait();
     tc::fence_before_sync();
+}
+
+// The cell's spectrum from the running total, scaled by `scale`, into hs (every entry written by
+// one operand thread).  Warp w reads lane quarter w & 3, i.e. A features 32 (w & 3) + l: the real
+// (l < 16) or imaginary (l >= 16) part of n-slot 16 (w & 3) + (l & 15), and the B modes
+// m' = 16 (w >> 2) .. + 15 (plus m' = 32 for w >> 2 == 1).  Lanes l and l ^ 16 exchange their
+// products; lane l < 16 writes the entries (m', n), lane l >= 16 the entries (-m', n).  A cell
+// without chunks (`empty`) gets zeros.
+__device__ __forceinline__ void tc_combine(unsigned tmem, cplx<float>* hs, int warp, int lane, int P, float scale,
+                                           bool empty) {
+    const int lq = warp & 3, hh = warp >> 2, half = P / 2;
+    const unsigned lanes = (unsigned)(32 * lq) << 16;
+    float vr[16], vi[16];
+    float xr = 0.0f, xi = 0.0f;
+    if (!empty) {
+        tc::tmem_ld16(tmem + lanes + total_col(32 * hh), vr);        // D[f][re m'],  m' = 16 hh + j
+        tc::tmem_ld16(tmem + lanes + total_col(32 * hh + 16), vi);   // D[f][im m']
+        if (hh == 1) {                                               // m' = 32
+            xr = tc::tmem_ld1(tmem + lanes + total_col(64));
+            xi = tc::tmem_ld1(tmem + lanes + total_col(72));
+        }
+        tc::tmem_ld_wait();
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) vr[j] = vi[j] = 0.0f;
+    }
+    const bool up = lane < 16;
+    const int ns = 16 * lq + (lane & 15);   // n-slot (n = ns - P/2)
+    cplx<float>* row = hs + ns * kHS;
+    const bool nrow = ns < P;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float pr = __shfl_xor_sync(0xffffffffu, vr[j], 16), pi = __shfl_xor_sync(0xffffffffu, vi[j], 16);
+        const int mp = 16 * hh + j;
+        // lane < 16: vr = P1, vi = P4, pr = P3, pi = P2;  lane >= 16: vr = P3, vi = P2, pr = P1, pi = P4
+        const bool ok = nrow && (up ? mp < half : (mp >= 1 && mp <= half));
+        const int col = up ? half + mp : half - mp;
+        const float re = up ? vr[j] - pi : pr + vi[j];
+        const float im = up ? pr + vi[j] : vr[j] - pi;
+        if (ok) row[col] = cplx<float>{re * scale, im * scale};
+    }
+    const float pr = __shfl_xor_sync(0xffffffffu, xr, 16), pi = __shfl_xor_sync(0xffffffffu, xi, 16);
+    if (hh == 1 && !up && nrow && half == 32)   // (-32, n): P1 + P2, P3 - P4
+        row[0] = cplx<float>{(pr + xi) * scale, (xr - pi) * scale};
 }
 
 template <bool FULL>
@@ -209,11 +274,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
     cplx<float>* hs = reinterpret_cast<cplx<float>*>(smem + kSpecOff);
     float* prep = reinterpret_cast<float*>(smem + kPrepOff);
     unsigned char* ems_sm = smem + kEmsOff;
-    unsigned long long* bar_mma = reinterpret_cast<unsigned long long*>(smem + kMiscOff);   // [2] MMAs done
-    unsigned long long* bar_full = bar_mma + 2;                                              // [2] operands written
-    unsigned long long* bar_prep = bar_mma + 4;                                              // [2] set-up ready
-    unsigned* tbase = reinterpret_cast<unsigned*>(smem + kMiscOff + 48);
-    float* red = reinterpret_cast<float*>(smem + kMiscOff + 64);   // 9 warps
+    unsigned long long* bar_mma = reinterpret_cast<unsigned long long*>(smem + kMiscOff);   // [4] MMAs done
+    unsigned long long* bar_full = bar_mma + kStages;                                        // [4] operands written
+    unsigned long long* bar_prep = bar_full + kStages;                                       // [4] set-up ready
+    unsigned long long* bar_pfree = bar_prep + kPrepBufs;                                    // [4] set-up read
+    unsigned* tbase = reinterpret_cast<unsigned*>(smem + kMiscOff + 128);
+    float* red = reinterpret_cast<float*>(smem + kMiscOff + 144);   // one per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = a.P, half = P / 2;
 
@@ -222,10 +288,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(tc::smem_addr(&bar_mma[s]), 1);
             tc::mbar_init(tc::smem_addr(&bar_full[s]), kFeatThreads);
-            tc::mbar_init(tc::smem_addr(&bar_prep[s]), 1);
+        }
+        for (int b = 0; b < kPrepBufs; ++b) {
+            tc::mbar_init(tc::smem_addr(&bar_prep[b]), 1);
+            tc::mbar_init(tc::smem_addr(&bar_pfree[b]), kFeatThreads / 32);
         }
         tc::mbar_init_fence();
     }
@@ -234,8 +303,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
     tc::fence_after_sync();
     const unsigned tmem = *tbase;
     const unsigned sbase = tc::smem_addr(smem);
-    const unsigned idesc = tc::idesc_f16_f32_mn(128, 128);
-    unsigned g = 0;   // chunks of this CTA so far (stage = g & 1, use of the stage = g >> 1)
+    const unsigned idesc = tc::idesc_f16_f32_mn(kFeatA, kFeatB);
+    unsigned g = 0;   // chunks of this CTA so far (stage g % 4, use g / 4 of the stage)
 
     for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
         const int cell = a.list[li];
@@ -266,7 +335,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
             }
         for (int o = 16; o; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
         if (lane == 0) red[warp] = cm;
-        for (int i = tid; i < 64 * kHS; i += kTcThreads) hs[i] = cplx<float>{0.0f, 0.0f};
         __syncthreads();
         cm = 0.0f;
         for (int i = 0; i < kTcThreads / 32; ++i) cm = fmaxf(cm, red[i]);
@@ -276,8 +344,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
         if (warp == kMmaWarp) {
             // ---- MMA warp: the three split products of each chunk once its operands are written
             for (int ch = 0; ch < nch; ++ch) {
-                const unsigned gc = g + ch, st = gc & 1u;
-                if (!tc::mbar_wait(tc::smem_addr(&bar_full[st]), (gc >> 1) & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
+                const unsigned gc = g + ch, st = gc % kStages;
+                if (!tc::mbar_wait(tc::smem_addr(&bar_full[st]), (gc / kStages) & 1u, kWaitLimit))
+                    atomicOr(a.status, ST_TIMEOUT);
                 tc::fence_after_sync();
                 if (lane == 0) {
                     const unsigned s0 = sbase + st * kStageBytes;
@@ -285,10 +354,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
                     const bool first = ch % kBlockChunks == 0;
 #pragma unroll
                     for (int s = 0; s < kCh / 16; ++s) {
-                        const uint64_t ah = tc::smem_desc(s0 + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                        const uint64_t al = tc::smem_desc(s0 + kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                        const uint64_t bh = tc::smem_desc(s0 + 2 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
-                        const uint64_t bl = tc::smem_desc(s0 + 3 * kOpBytes + s * 4096, tc::kTcLbo, tc::kTcSbo);
+                        const uint64_t ah = tc::smem_desc(s0 + s * LayA::kKStep, LayA::kLbo, LayA::kSbo);
+                        const uint64_t al = tc::smem_desc(s0 + kOpA + s * LayA::kKStep, LayA::kLbo, LayA::kSbo);
+                        const uint64_t bh = tc::smem_desc(s0 + 2 * kOpA + s * LayB::kKStep, LayB::kLbo, LayB::kSbo);
+                        const uint64_t bl = tc::smem_desc(s0 + 2 * kOpA + kOpB + s * LayB::kKStep, LayB::kLbo, LayB::kSbo);
                         tc::mma_f16(acc, ah, bh, idesc, (!first || s > 0) ? 1u : 0u);
                         tc::mma_f16(acc, ah, bl, idesc, 1u);
                         tc::mma_f16(acc, al, bh, idesc, 1u);
@@ -298,8 +367,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
                 __syncwarp();
             }
         } else if (warp >= kPrepWarp0) {
-            // ---- set-up warp of stage sp: chunks ch with (g + ch) & 1 == sp, each into the stage's
-            // set-up buffer once the operand warps have written the chunk two before (which read it)
+            // ---- set-up warp sp: chunks ch with (g + ch) & 1 == sp, each into set-up buffer
+            // (g + ch) % 4 once the operand warps have read the chunk four before from it
             const unsigned sp = (unsigned)(warp - kPrepWarp0);
             const FastFrame ff = fast_frame(cc);
             const float inv_nf = 1.0f / (float)a.NF;
@@ -318,60 +387,99 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
             const int c0 = (int)((sp - g) & 1u);
             if (c0 < nch) load(c0);
             for (int ch = c0; ch < nch; ch += 2) {
-                const unsigned gc = g + ch;
-                if (ch >= 2 && !tc::mbar_wait(tc::smem_addr(&bar_full[sp]), ((gc - 2) >> 1) & 1u, kWaitLimit))
+                const unsigned gc = g + ch, b = gc % kPrepBufs;
+                if (gc >= kPrepBufs &&
+                    !tc::mbar_wait(tc::smem_addr(&bar_pfree[b]), (gc / kPrepBufs - 1) & 1u, kWaitLimit))
                     atomicOr(a.status, ST_TIMEOUT);
-                tc_prep_sample(ff, cc, rv, rx, ry, rh, rw, inv_cm, inv_nf, prep + sp * kPrepF * kCh, lane, a.status);
+                tc_prep_sample(ff, cc, rv, rx, ry, rh, rw, inv_cm, inv_nf, prep + b * kPrepF * kCh, lane, a.status);
                 if (ch + 2 < nch) load(ch + 2);
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_prep[sp]));
+                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_prep[b]));
             }
         } else {
             // ---- operand warps
             const int k = (lane & 7) + 8 * (warp & 3), o = (lane >> 3) + 4 * (warp >> 2);
             for (int ch = 0; ch < nch; ++ch) {
-                const unsigned gc = g + ch, st = gc & 1u, use = gc >> 1;
-                if (!tc::mbar_wait(tc::smem_addr(&bar_prep[st]), use & 1u, kWaitLimit)) atomicOr(a.status, ST_TIMEOUT);
+                const unsigned gc = g + ch, st = gc % kStages, use = gc / kStages, b = gc % kPrepBufs;
                 if (use > 0 && !tc::mbar_wait(tc::smem_addr(&bar_mma[st]), (use - 1) & 1u, kWaitLimit))
                     atomicOr(a.status, ST_TIMEOUT);
                 if (ch >= 2 * kBlockChunks && ch % kBlockChunks == 0) {
                     // the run two blocks back is complete (the stage wait covers every earlier MMA):
-                    // add it to the staged spectrum before its bank is reused
+                    // add it to the running total before its bank is reused
                     tc::fence_after_sync();
-                    tc_flush(tmem + 128u * ((ch / kBlockChunks) & 1), hs, warp, lane);
+                    tc_accumulate(tmem, 128u * ((ch / kBlockChunks) & 1), warp, ch == 2 * kBlockChunks);
                 }
-                const float* pr = prep + st * kPrepF * kCh;
+                // this chunk's set-up values into registers; the buffer is then free for the set-up warps
+                if (!tc::mbar_wait(tc::smem_addr(&bar_prep[b]), (gc / kPrepBufs) & 1u, kWaitLimit))
+                    atomicOr(a.status, ST_TIMEOUT);
+                const float* pr = prep + b * kPrepF * kCh;
+                const float ca = pr[k], tya = pr[3 * kCh + k], tyl = pr[4 * kCh + k], wya = pr[7 * kCh + k],
+                            wyi = pr[8 * kCh + k];
+                float txa = 0.f, txl = 0.f, wxa = 0.f, wxi = 0.f;
+                if (warp < 4) {
+                    txa = pr[1 * kCh + k];
+                    txl = pr[2 * kCh + k];
+                    wxa = pr[5 * kCh + k];
+                    wxi = pr[6 * kCh + k];
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_pfree[b]));
                 unsigned char* stg = smem + st * kStageBytes;
-#pragma unroll
-                for (int ax = 0; ax < 2; ++ax) {   // axis 0 -> A (y, times c), 1 -> B (x)
-                    const float th = pr[(ax ? 1 : 3) * kCh + k], tl = pr[(ax ? 2 : 4) * kCh + k];
-                    const float wr = pr[(ax ? 5 : 7) * kCh + k], wi = pr[(ax ? 6 : 8) * kCh + k];
-                    float re[8], im[8];
-                    tc_phasors<FULL>(th, tl, wr, wi, ax ? 1.0f : pr[k], 8 * o - half, 8 * o, P, re, im);
+                {   // A: modes n = 8 o - P/2 .. + 7 (y), times the scaled weight
+                    float re[8], im[8], r8, i8;
+                    tc_phasors<FULL>(tya, tyl, wya, wyi, ca, 8 * o - half, 8 * o, P, re, im, r8, i8);
                     uint4 rh, rl, ih, il;
                     tc_split8(re, rh, rl);
                     tc_split8(im, ih, il);
-                    unsigned char* hi = stg + (ax ? 2 : 0) * kOpBytes;
-                    unsigned char* lo = hi + kOpBytes;
-                    *reinterpret_cast<uint4*>(hi + tc::tc_off(8 * o, k)) = rh;
-                    *reinterpret_cast<uint4*>(lo + tc::tc_off(8 * o, k)) = rl;
-                    *reinterpret_cast<uint4*>(hi + tc::tc_off(64 + 8 * o, k)) = ih;
-                    *reinterpret_cast<uint4*>(lo + tc::tc_off(64 + 8 * o, k)) = il;
+                    const unsigned fr = LayA::off(feat_re(o), k), fi = LayA::off(feat_re(o) + 16, k);
+                    *reinterpret_cast<uint4*>(stg + fr) = rh;
+                    *reinterpret_cast<uint4*>(stg + kOpA + fr) = rl;
+                    *reinterpret_cast<uint4*>(stg + fi) = ih;
+                    *reinterpret_cast<uint4*>(stg + kOpA + fi) = il;
+                }
+                if (warp < 4) {   // B: modes m' = 8 o .. 8 o + 7 (x), o < 4; octet 3 also writes m' = 32 .. 39
+                    float re[8], im[8], r8, i8;
+                    tc_phasors<FULL>(txa, txl, wxa, wxi, 1.0f, 8 * o, 8 * o, half + 1, re, im, r8, i8);
+                    uint4 rh, rl, ih, il;
+                    tc_split8(re, rh, rl);
+                    tc_split8(im, ih, il);
+                    unsigned char* bhi = stg + 2 * kOpA;
+                    const unsigned fr = LayB::off(feat_re(o), k), fi = LayB::off(feat_im_b(o), k);
+                    *reinterpret_cast<uint4*>(bhi + fr) = rh;
+                    *reinterpret_cast<uint4*>(bhi + kOpB + fr) = rl;
+                    *reinterpret_cast<uint4*>(bhi + fi) = ih;
+                    *reinterpret_cast<uint4*>(bhi + kOpB + fi) = il;
+                    if (o == 3) {   // m' = 32 (P = 64 only) followed by seven zero features
+                        const float e = FULL ? r8 : 0.0f, f = FULL ? i8 : 0.0f;
+                        const __half eh = __float2half_rn(e), fh = __float2half_rn(f);
+                        const __half el = __float2half_rn(e - __half2float(eh)), fl = __float2half_rn(f - __half2float(fh));
+                        rh = make_uint4(__half_as_ushort(eh), 0u, 0u, 0u);
+                        rl = make_uint4(__half_as_ushort(el), 0u, 0u, 0u);
+                        ih = make_uint4(__half_as_ushort(fh), 0u, 0u, 0u);
+                        il = make_uint4(__half_as_ushort(fl), 0u, 0u, 0u);
+                        const unsigned gr = LayB::off(feat_re(4), k), gi = LayB::off(feat_im_b(4), k);
+                        *reinterpret_cast<uint4*>(bhi + gr) = rh;
+                        *reinterpret_cast<uint4*>(bhi + kOpB + gr) = rl;
+                        *reinterpret_cast<uint4*>(bhi + gi) = ih;
+                        *reinterpret_cast<uint4*>(bhi + kOpB + gi) = il;
+                    }
                 }
                 tc::fence_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(tc::smem_addr(&bar_full[st]));
             }
-            // ---- the last one or two runs -> staged spectrum, scaled back by max |c|
+            // ---- the last one or two runs into the total; once every MMA is done the stage memory is
+            // free and takes the spectrum, scaled back by max |c|
             if (nch > 0) {
                 const unsigned gl = g + nch - 1;
-                if (!tc::mbar_wait(tc::smem_addr(&bar_mma[gl & 1u]), (gl >> 1) & 1u, kWaitLimit))
+                if (!tc::mbar_wait(tc::smem_addr(&bar_mma[gl % kStages]), (gl / kStages) & 1u, kWaitLimit))
                     atomicOr(a.status, ST_TIMEOUT);
                 tc::fence_after_sync();
                 const int nb = (nch + kBlockChunks - 1) / kBlockChunks;
-                for (int b = nb >= 2 ? nb - 2 : 0; b < nb; ++b) tc_flush(tmem + 128u * (b & 1), hs, warp, lane);
-                for (int i = tid; i < 64 * kHS; i += kFeatThreads) hs[i] = cplx<float>{hs[i].re * cm, hs[i].im * cm};
+                for (int b = nb >= 2 ? nb - 2 : 0; b < nb; ++b)
+                    tc_accumulate(tmem, 128u * (b & 1), warp, b == 0);
             }
+            tc_combine(tmem, hs, warp, lane, P, cm, nch == 0);
         }
         g += (unsigned)nch;
         tc::fence_before_sync();
