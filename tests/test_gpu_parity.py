@@ -100,18 +100,19 @@ def test_type1_masks_and_edge_cases():
         assert err.max() <= 1e-5, (mask, err)
 
 
-def test_samples_on_window_boundary_follow_the_binary64_decision():
+@pytest.mark.parametrize("nb", [40, 300])
+def test_samples_on_window_boundary_follow_the_binary64_decision(nb):
     """Samples placed on (and within rounding of) the cell edges and the square's sides are kept or
-    dropped exactly as the binary64 definition decides (closed mask)."""
+    dropped exactly as the binary64 definition decides (closed mask); a few or many of them."""
     wl = synth.make("tri20480_p64", seed=4, n_cells=2, q_scale=0.1, dtype=torch.float64)
     V = wl.verts[0, :3].numpy()
     rng = np.random.default_rng(0)
-    t = rng.random(300)
-    e = rng.integers(0, 3, 300)
+    t = rng.random(nb)
+    e = rng.integers(0, 3, nb)
     pts = V[e] + t[:, None] * (V[(e + 1) % 3] - V[e])
     pts += rng.standard_normal(pts.shape) * 1e-7          # straddle the edges
     a, b = int(wl.offsets[0]), int(wl.offsets[1])
-    n = min(300, b - a)
+    n = min(nb, b - a)
     wl.x[a:a + n] = torch.tensor(pts[:n, 0])
     wl.y[a:a + n] = torch.tensor(pts[:n, 1])
     wl32 = synth.Workload(**{**wl.__dict__, "x": wl.x.float(), "y": wl.y.float(), "h": wl.h.float(),
