@@ -436,7 +436,7 @@ def run_ours(args):
 
     # the same step with the routes tuned at plan creation (threshold at most the workload's cap)
     tuned = None
-    if not args.no_tune and info["cells_large"] == 0 and wl.x.dtype == torch.float32:
+    if not args.no_tune and wl.x.dtype == torch.float32:   # routes (fused / tensor core) or the n_f = 256 tile
         tplan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame, autotune=True)
         tinfo = tplan.info()
         tco = tplan.new_coeffs()
@@ -446,7 +446,7 @@ def run_ours(args):
         tplan.sync_status()
         tuned = {"ms_per_step": tms, "value": pts_all / (tms * 1e-3), "unit": "points/s",
                  "tuning": tplan.tuning(), "cells_tensor_core": tinfo["cells_tensor"],
-                 "cells_fused": tinfo["cells_fused"]}
+                 "cells_fused": tinfo["cells_fused"], "large_tile": tinfo["large_tile"]}
         del tg, tplan, tco, tout
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -661,6 +661,7 @@ def run_ours(args):
                            **({"max_q": args.max_q} if args.max_q is not None else {}),
                            **({"cells_subset": args.cells} if args.cells is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
+                           "large_tile": info["large_tile"],
                            "kernel": args.kernel, "frame": args.frame, "precision": "mixed",
                            "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
                            "timing": "one replay per step of the plan-owned CUDA graph of enufft_type1_ems (enufft_type1_ems_graph)",

@@ -103,9 +103,9 @@ typedef struct {
     enufft_frame frame;   /* local frame orientation (default CENTROID)                          */
     int autotune;         /* 1: tune the execution routes at plan creation (see enufft_tuning):
                              the tensor-core routing threshold, at most tc_max_points, and the
-                             fused kernel's blocks per SM; 0 (default): take tc_max_points as
-                             given.  Mixed-precision plans of the fused / tensor-core routes
-                             only; elsewhere it has no effect                                    */
+                             fused kernel's blocks per SM, or for n_f = 256 plans the tile side of
+                             the sorted spreading; 0 (default): take tc_max_points as given and
+                             tiles of 32.  Mixed-precision plans only; elsewhere it has no effect */
     const char *tune_cache;   /* NULL, or a JSON file of earlier tunings (read, and written on a
                                  miss) keyed by GPU name, SM count, P, n_f, w, precision, kernel,
                                  frame and tc_max_points                                        */
@@ -330,6 +330,8 @@ typedef struct {
     int tc_max_points;                 /* routing threshold in effect (tuned or as given)       */
     int autotuned;                     /* 1 if the routes were tuned at plan creation           */
     int fused_blocks_per_sm;           /* persistent blocks per SM of the fused kernel          */
+    int large_tile;                    /* n_f = 256 route: tile side of its sorted spreading
+                                          (16, 32 or 64; 0 for other routes)                     */
 } enufft_plan_info;
 enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
 
@@ -340,8 +342,11 @@ enufft_status enufft_get_plan_info(enufft_plan plan, enufft_plan_info *info);
  * window), the fused spread/FFT kernel against the tensor-core direct sum at Q = 128, 256, 512,
  * 1024, 2048, 3072, 4096, 6144 (those not above tc_max_points) and keeps as threshold the largest Q
  * at which the direct sum was faster per sample (0 = none); and the fused kernel with one against
- * two resident blocks per SM, at the plan's median cell size.  Results are identical either way
- * within the accuracy of each route; only the time changes.
+ * two resident blocks per SM, at the plan's median cell size.  For n_f = 256 plans it instead times
+ * the sorted tile spreading of the plan's first batch (its own cells, synthetic samples) with tiles
+ * of 16, 32 and 64 nodes and keeps the fastest: then ladder[] holds the sides tried and ns_fused[]
+ * the route's ns per sample with each.  Results are identical either way within the accuracy of
+ * each route; only the time changes.
  *   ladder[i], ns_fused[i], ns_tc[i]: the measured ns per sample of each route at Q = ladder[i]
  *   from_cache: 1 if the record was read from opts.tune_cache instead of measured
  */
@@ -353,6 +358,7 @@ typedef struct {
     double ns_fused[8];
     double ns_tc[8];
     int from_cache;
+    int large_tile;   /* n_f = 256 plans: the tile side kept (0 in records of other plans) */
 } enufft_tuning;
 /* The plan's tuning record; ENUFFT_ERR_ARG if the plan was not tuned. */
 enufft_status enufft_get_tuning(enufft_plan plan, enufft_tuning *out);

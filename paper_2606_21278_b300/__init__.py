@@ -50,20 +50,20 @@ class _Info(ctypes.Structure):
                 ("cells_tensor", ctypes.c_int64), ("cells_large", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("cells_plain", ctypes.c_int64), ("kernels_per_type1_ems", ctypes.c_int64),
                 ("kernel", ctypes.c_int), ("frame", ctypes.c_int), ("tc_max_points", ctypes.c_int),
-                ("autotuned", ctypes.c_int), ("fused_blocks_per_sm", ctypes.c_int)]
+                ("autotuned", ctypes.c_int), ("fused_blocks_per_sm", ctypes.c_int), ("large_tile", ctypes.c_int)]
 
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("tc_max_points", ctypes.c_int), ("fused_blocks_per_sm", ctypes.c_int), ("n_ladder", ctypes.c_int),
                 ("ladder", ctypes.c_int * 8), ("ns_fused", ctypes.c_double * 8), ("ns_tc", ctypes.c_double * 8),
-                ("from_cache", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("large_tile", ctypes.c_int)]
 
 
 def _tuning_dict(t: _Tuning) -> dict:
     n = t.n_ladder
     return {"tc_max_points": t.tc_max_points, "fused_blocks_per_sm": t.fused_blocks_per_sm,
             "ladder": list(t.ladder[:n]), "ns_fused": list(t.ns_fused[:n]), "ns_tc": list(t.ns_tc[:n]),
-            "from_cache": bool(t.from_cache)}
+            "from_cache": bool(t.from_cache), "large_tile": t.large_tile}
 
 
 def load_library(path: str = LIB_PATH):
@@ -379,6 +379,7 @@ def tune_cache_store(path: str, key: str, rec: dict) -> None:
     t = _Tuning()
     t.tc_max_points = int(rec["tc_max_points"])
     t.fused_blocks_per_sm = int(rec["fused_blocks_per_sm"])
+    t.large_tile = int(rec.get("large_tile", 0))
     n = len(rec.get("ladder", []))
     t.n_ladder = n
     for i in range(n):

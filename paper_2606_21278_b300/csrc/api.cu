@@ -112,6 +112,7 @@ struct enufft_plan_s {
     double* d_lpartial = nullptr;            // reconstruction: per work item partial sums [max items][3]
     double* d_lspec = nullptr;               // reconstruction: per cell spectral variances [n_cells][2]
     int lmax_cells = 0;
+    int lt = kLT;                            // tile side of the sorted spreading (16, 32 or 64)
     // edge-aligned frame: per-cell centroid and rotation, per-call local coordinates of the samples
     bool edge = false;
     FrameRot* d_rot = nullptr;
@@ -137,6 +138,21 @@ struct enufft_plan_s {
     GraphKey gkey = {};
     std::string err;
 };
+
+static enufft_status tune_large_tile(enufft_plan p, const std::vector<int64_t>& off, enufft_tuning* t);
+
+// key of a plan configuration in the tuning cache: the configuration on this kind of GPU
+static std::string tune_key(enufft_plan p, const enufft_opts& o, int NF, int W) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->device);
+    std::string gpu = prop.name;
+    for (char& c : gpu)
+        if (c == '"' || c == '\\') c = '_';
+    char key[384];
+    snprintf(key, sizeof key, "gpu=%s|sms=%d|P=%d|nf=%d|w=%d|prec=%d|kernel=%d|frame=%d|tc_cap=%d", gpu.c_str(),
+             p->num_sms, p->P, NF, W, (int)o.prec, (int)o.kernel, (int)o.frame, o.tc_max_points);
+    return key;
+}
 
 // batch bounds of the large route: records (16 B per sample) and fine grids (256 KB per cell)
 static constexpr int64_t kLargeBatchPoints = (int64_t)1 << 26;
@@ -546,6 +562,24 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
             return st;
         }
         p->n_fused = 0;
+        if (o.autotune && n_cells > 0 && !p->lbatches.empty()) {
+            const std::string key = tune_key(p, o, NF, W);
+            enufft_tuning t;
+            if (!(o.tune_cache && tune_cache_get(o.tune_cache, key, &t) &&
+                  (t.large_tile == 16 || t.large_tile == 32 || t.large_tile == 64))) {
+                const enufft_status st = tune_large_tile(p, off, &t);
+                if (st != ENUFFT_OK) {
+                    enufft_plan_destroy(p);
+                    return st;
+                }
+                cudaMemsetAsync(p->d_ctr + 2, 0, sizeof(unsigned), p->stream);   // the trial runs leave no status
+                cudaStreamSynchronize(p->stream);
+                if (o.tune_cache) tune_cache_put(o.tune_cache, key, t);   // best effort
+            }
+            p->tuned = true;
+            p->tuning = t;
+            p->lt = t.large_tile;
+        }
         *out = p;
         return ENUFFT_OK;
     }
@@ -595,8 +629,8 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
         if ((e = cudaMalloc(&p->d_lblocks, sizeof(int4) * std::max<size_t>(blocks.size(), 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lcellblk, sizeof(int2) * cellblk.size())) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lwork, sizeof(int4) * std::max<size_t>(work.size(), 1))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_lblk_off, sizeof(int) * (kLTiles + 1) * std::max(max_blocks, 1))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTiles * std::max(max_blocks, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lblk_off, sizeof(int) * (kLTilesMax + 1) * std::max(max_blocks, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_lblk_abs, sizeof(float) * kLTilesMax * std::max(max_blocks, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lrec, sizeof(float4) * std::max<int64_t>(max_pts, 1))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lgrid, sizeof(unsigned long long) * kLNF * kLNF * mc)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_lexp, sizeof(int) * mc)) != cudaSuccess ||
@@ -623,6 +657,24 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
             return st;
         }
         p->n_fused = 0;
+        if (o.autotune && n_cells > 0 && !p->lbatches.empty()) {
+            const std::string key = tune_key(p, o, NF, W);
+            enufft_tuning t;
+            if (!(o.tune_cache && tune_cache_get(o.tune_cache, key, &t) &&
+                  (t.large_tile == 16 || t.large_tile == 32 || t.large_tile == 64))) {
+                const enufft_status st = tune_large_tile(p, off, &t);
+                if (st != ENUFFT_OK) {
+                    enufft_plan_destroy(p);
+                    return st;
+                }
+                cudaMemsetAsync(p->d_ctr + 2, 0, sizeof(unsigned), p->stream);   // the trial runs leave no status
+                cudaStreamSynchronize(p->stream);
+                if (o.tune_cache) tune_cache_put(o.tune_cache, key, t);   // best effort
+            }
+            p->tuned = true;
+            p->tuning = t;
+            p->lt = t.large_tile;
+        }
         *out = p;
         return ENUFFT_OK;
     }
@@ -640,15 +692,7 @@ enufft_status enufft_plan_create(enufft_plan* out, const enufft_opts* opts, int6
     }
     p->fwd_grid_per_sm = p->fwd_per_sm;
     if (o.autotune && !p->dbl && n_cells > 0) {
-        // key: the configuration on this kind of GPU
-        cudaDeviceProp prop;
-        cudaGetDeviceProperties(&prop, p->device);
-        std::string gpu = prop.name;
-        for (char& c : gpu)
-            if (c == '"' || c == '\\') c = '_';
-        char key[384];
-        snprintf(key, sizeof key, "gpu=%s|sms=%d|P=%d|nf=%d|w=%d|prec=%d|kernel=%d|frame=%d|tc_cap=%d", gpu.c_str(),
-                 p->num_sms, p->P, NF, W, (int)o.prec, (int)o.kernel, (int)o.frame, o.tc_max_points);
+        const std::string key = tune_key(p, o, NF, W);
         enufft_tuning t;
         if (!(o.tune_cache && tune_cache_get(o.tune_cache, key, &t))) {
             std::vector<int64_t> q(n_cells);
@@ -704,6 +748,7 @@ enufft_status enufft_get_plan_info(enufft_plan p, enufft_plan_info* info) {
     info->tc_max_points = p->n_tc > 0 || p->tuned ? p->tc_threshold : 0;
     info->autotuned = p->tuned ? 1 : 0;
     info->fused_blocks_per_sm = p->fwd_grid_per_sm;
+    info->large_tile = p->large ? p->lt : 0;
     int64_t k = 0;
     if (p->plain) {
         for (int64_t j = 0; j < p->n_cells; ++j) k += p->h_off[j + 1] > p->h_off[j] ? 4 : 3;
@@ -811,8 +856,9 @@ static enufft_status launch_ems(enufft_plan p, const void* d_coeffs, const EmsAr
     return e == cudaSuccess ? ENUFFT_OK : cuda_fail(p, e, "ems: finish launch");
 }
 
-static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
-                                     void* coeffs, const EmsArgs* ems) {
+// the batches [0, nbatch) of the large route with tile side lt
+static enufft_status run_large_batches(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
+                                       void* coeffs, const EmsArgs* ems, int lt, size_t nbatch) {
     LargeArgs la;
     memset(&la, 0, sizeof(la));
     la.x = (const float*)x;
@@ -838,7 +884,8 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
     fa.do_ems = ems ? 1 : 0;
     if (ems) fa.ems = *ems;
     fa.ems_out = p->ems_scratch;
-    for (const auto& b : p->lbatches) {
+    for (size_t bi = 0; bi < nbatch && bi < p->lbatches.size(); ++bi) {
+        const auto& b = p->lbatches[bi];
         la.cell0 = fa.cell0 = b.cell0;
         la.ncells = fa.ncells = b.ncells;
         la.p0 = b.p0;
@@ -848,7 +895,8 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
         cudaError_t e = cudaMemsetAsync(p->d_lgrid, 0, sizeof(unsigned long long) * kLNF * kLNF * (size_t)b.ncells,
                                         p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): memset");
-        e = large_run_batch(la, std::max(b.nblocks, 0), b.nwork, fa, p->W, std::min(b.ncells, p->num_sms), p->stream);
+        e = large_run_batch(la, std::max(b.nblocks, 0), b.nwork, fa, p->W, lt, std::min(b.ncells, p->num_sms),
+                            p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "type1 (large): launch");
     }
     if (ems) {
@@ -857,6 +905,67 @@ static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y
         if (e != cudaSuccess) return cuda_fail(p, e, "type1_ems (large): finish launch");
     }
     return ENUFFT_OK;
+}
+
+static enufft_status run_type1_large(enufft_plan p, const void* x, const void* y, const void* h, const void* w,
+                                     void* coeffs, const EmsArgs* ems) {
+    return run_large_batches(p, x, y, h, w, coeffs, ems, p->lt, p->lbatches.size());
+}
+
+// Tile side of the large route by measurement (opts.autotune): the plan's first batch with
+// synthetic samples (uniform over each cell's window) run with tiles of 16, 32 and 64; the record
+// keeps the sides tried in ladder[] and the route's ns per sample with each in ns_fused[].
+static enufft_status tune_large_tile(enufft_plan p, const std::vector<int64_t>& off, enufft_tuning* t) {
+    memset(t, 0, sizeof(*t));
+    t->fused_blocks_per_sm = 1;
+    t->large_tile = kLT;
+    const auto& b = p->lbatches[0];
+    const int64_t npts = off[b.cell0 + b.ncells] - b.p0;
+    if (npts <= 0) return ENUFFT_OK;
+    float *x = nullptr, *y = nullptr, *h = nullptr, *w = nullptr;
+    void* co = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    enufft_status st = ENUFFT_OK;
+    if ((e = cudaMalloc(&x, 4 * (size_t)npts)) != cudaSuccess || (e = cudaMalloc(&y, 4 * (size_t)npts)) != cudaSuccess ||
+        (e = cudaMalloc(&h, 4 * (size_t)npts)) != cudaSuccess || (e = cudaMalloc(&w, 4 * (size_t)npts)) != cudaSuccess ||
+        (e = cudaMalloc(&co, sizeof(cplx<float>) * (size_t)p->P * p->P * (b.cell0 + b.ncells))) != cudaSuccess ||
+        (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+        (e = large_tune_samples(p->d_cells + b.cell0, p->d_offsets + b.cell0, b.p0, b.ncells, x, y, h, w,
+                                p->stream)) != cudaSuccess) {
+        st = cuda_fail(nullptr, e, "plan_create: tile tuning");
+    } else {
+        double best = 1e30;
+        const int sides[3] = {16, 32, 64};
+        t->n_ladder = 3;
+        for (int i = 0; i < 3 && st == ENUFFT_OK; ++i) {
+            double ms_best = 1e30;
+            for (int rep = 0; rep < 3 && st == ENUFFT_OK; ++rep) {   // a warm-up, then the best of two
+                cudaEventRecord(e0, p->stream);
+                st = run_large_batches(p, x, y, h, w, co, nullptr, sides[i], 1);
+                cudaEventRecord(e1, p->stream);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(nullptr, e, "plan_create: tile tuning");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_best = std::min(ms_best, (double)ms);
+            }
+            t->ladder[i] = sides[i];
+            t->ns_fused[i] = ms_best * 1e6 / (double)npts;
+            if (ms_best < best) {
+                best = ms_best;
+                t->large_tile = sides[i];
+            }
+        }
+        if (st != ENUFFT_OK) st = fail(nullptr, st, std::string("plan_create: tile tuning: ") + p->err);
+    }
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(h);
+    cudaFree(w);
+    cudaFree(co);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
 }
 
 static enufft_status run_type1_plain(enufft_plan p, const void* x, const void* y, const void* h, const void* w,

@@ -53,12 +53,11 @@ __global__ void tune_gather_cells(const CellConst* __restrict__ src, int n_src, 
 // Q samples per synthetic cell, uniform over the window of its frame (cell mask: rejection from the
 // polygon's bounding box, up to 32 draws, the centroid as the last resort), elevation a smooth
 // field of a few hundred metres, weight |D| / Q
-__global__ void tune_samples(const CellConst* __restrict__ cells, int n, int Q, float* __restrict__ x,
-                             float* __restrict__ y, float* __restrict__ h, float* __restrict__ w) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * Q) return;
-    const int c = (int)(idx / Q);
-    const CellConst& cc = cells[c];
+// sample idx of a cell with Q samples: uniform over the cell's window (rejection from its bounding
+// box with a counter-based hash), a smooth elevation, weights |D| / Q
+__device__ __forceinline__ void tune_sample(const CellConst& cc, int64_t idx, int64_t Q, float* __restrict__ x,
+                                            float* __restrict__ y, float* __restrict__ h, float* __restrict__ w,
+                                            int64_t out) {
     double lox = -cc.H, hix = cc.H, loy = -cc.H, hiy = cc.H;
     if (cc.mask == 0 && cc.nv >= 3) {
         lox = hix = cc.ux[0];
@@ -87,10 +86,27 @@ __global__ void tune_samples(const CellConst* __restrict__ cells, int n, int Q, 
             break;
         }
     }
-    x[idx] = (float)(cc.cx + ux);
-    y[idx] = (float)(cc.cy + uy);
-    h[idx] = (float)(300.0 + 400.0 * sin(9.0 * ux / cc.H) * cos(7.0 * uy / cc.H));
-    w[idx] = (float)(cc.area / Q);
+    x[out] = (float)(cc.cx + ux);
+    y[out] = (float)(cc.cy + uy);
+    h[out] = (float)(300.0 + 400.0 * sin(9.0 * ux / cc.H) * cos(7.0 * uy / cc.H));
+    w[out] = (float)(cc.area / (double)Q);
+}
+
+__global__ void tune_samples(const CellConst* __restrict__ cells, int n, int Q, float* __restrict__ x,
+                             float* __restrict__ y, float* __restrict__ h, float* __restrict__ w) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * Q) return;
+    tune_sample(cells[idx / Q], idx, Q, x, y, h, w, idx);
+}
+
+// the same for cells with their own counts (offsets relative to p0), one block per cell
+__global__ void tune_samples_off(const CellConst* __restrict__ cells, const int64_t* __restrict__ offsets, int64_t p0,
+                                 float* __restrict__ x, float* __restrict__ y, float* __restrict__ h,
+                                 float* __restrict__ w) {
+    const int c = blockIdx.x;
+    const int64_t q0 = offsets[c], q1 = offsets[c + 1];
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+        tune_sample(cells[c], q, q1 - q0, x, y, h, w, q - p0);
 }
 
 struct Dev {
@@ -329,7 +345,8 @@ int field_arr(const std::string& obj, const char* name, double* v, int cap) {
 
 std::string tuning_json(const enufft_tuning& t) {
     std::string s = "{\"tc_max_points\": " + std::to_string(t.tc_max_points) +
-                    ", \"fused_blocks_per_sm\": " + std::to_string(t.fused_blocks_per_sm) + ", \"ladder\": [";
+                    ", \"fused_blocks_per_sm\": " + std::to_string(t.fused_blocks_per_sm) +
+                    ", \"large_tile\": " + std::to_string(t.large_tile) + ", \"ladder\": [";
     char buf[64];
     for (int i = 0; i < t.n_ladder; ++i) s += (i ? ", " : "") + std::to_string(t.ladder[i]);
     s += "], \"ns_fused\": [";
@@ -357,6 +374,13 @@ bool read_file(const char* path, std::string& s) {
 
 }  // namespace
 
+cudaError_t large_tune_samples(const CellConst* cells, const int64_t* offsets, int64_t p0, int ncells, float* x,
+                               float* y, float* h, float* w, cudaStream_t s) {
+    if (ncells <= 0) return cudaSuccess;
+    tune_samples_off<<<ncells, kTuneThreads, 0, s>>>(cells, offsets, p0, x, y, h, w);
+    return cudaGetLastError();
+}
+
 bool tune_cache_get(const char* path, const std::string& key, enufft_tuning* out) {
     std::string s;
     std::map<std::string, std::string> m;
@@ -377,6 +401,7 @@ bool tune_cache_get(const char* path, const std::string& key, enufft_tuning* out
     for (int i = 0; i < nl; ++i) t.ladder[i] = (int)a[i];
     if (field_arr(it->second, "ns_fused", t.ns_fused, 8) != nl || field_arr(it->second, "ns_tc", t.ns_tc, 8) != nl)
         return false;
+    t.large_tile = field_num(it->second, "large_tile", v) ? (int)v : 0;   // older records: none
     if (t.tc_max_points < 0 || t.fused_blocks_per_sm < 1) return false;
     t.from_cache = 1;
     *out = t;

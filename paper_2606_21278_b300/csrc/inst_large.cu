@@ -44,26 +44,39 @@ cudaError_t large_run_adjoint_batch(const LargeAdjFftArgs& fa, const LargeInterp
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, int LT>
 static void launch_spread(const LargeArgs& la, int nblocks, cudaStream_t s) {
-    large_spread_kernel<W><<<nblocks, kLSpreadThreads, 0, s>>>(la);
+    large_spread_kernel<W, LT><<<nblocks, kLSpreadThreads, 0, s>>>(la);
 }
 
-cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
-                            int fft_grid, cudaStream_t s) {
-    if (la.ncells <= 0) return cudaSuccess;
-    if (nbin_blocks > 0) large_sort_kernel<<<nbin_blocks, kLSortThreads, 0, s>>>(la);
+template <int LT>
+static cudaError_t run_batch_tiles(const LargeArgs& la, int nbin_blocks, int nwork, int W, cudaStream_t s) {
+    if (nbin_blocks > 0) large_sort_kernel<LT><<<nbin_blocks, kLSortThreads, 0, s>>>(la);
     constexpr int cells_per_block = kLScaleThreads / 32;
-    large_scale_kernel<<<(la.ncells + cells_per_block - 1) / cells_per_block, kLScaleThreads, 0, s>>>(la);
-    const int nt = nwork * kLTiles;
+    large_scale_kernel<LT><<<(la.ncells + cells_per_block - 1) / cells_per_block, kLScaleThreads, 0, s>>>(la);
+    const int nt = nwork * large_tiles(LT);
     switch (W) {
-        case 4: launch_spread<4>(la, nt, s); break;
-        case 5: launch_spread<5>(la, nt, s); break;
-        case 6: launch_spread<6>(la, nt, s); break;
-        case 7: launch_spread<7>(la, nt, s); break;
-        case 8: launch_spread<8>(la, nt, s); break;
+        case 4: launch_spread<4, LT>(la, nt, s); break;
+        case 5: launch_spread<5, LT>(la, nt, s); break;
+        case 6: launch_spread<6, LT>(la, nt, s); break;
+        case 7: launch_spread<7, LT>(la, nt, s); break;
+        case 8: launch_spread<8, LT>(la, nt, s); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaSuccess;
+}
+
+cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W, int lt,
+                            int fft_grid, cudaStream_t s) {
+    if (la.ncells <= 0) return cudaSuccess;
+    cudaError_t e;
+    switch (lt) {
+        case 16: e = run_batch_tiles<16>(la, nbin_blocks, nwork, W, s); break;
+        case 32: e = run_batch_tiles<32>(la, nbin_blocks, nwork, W, s); break;
+        case 64: e = run_batch_tiles<64>(la, nbin_blocks, nwork, W, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
     large_fft_kernel<<<fft_grid, kLFftThreads, large_fft_smem_bytes(fa.P), s>>>(fa);
     return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ cudaError_t launch_adjoint(const AdjArgs<double>& a, int nf, int w, int grid, cu
 struct LargeArgs;
 struct LargeFftArgs;
 cudaError_t large_prepare(int P);
-cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W,
+cudaError_t large_run_batch(const LargeArgs& la, int nbin_blocks, int nwork, const LargeFftArgs& fa, int W, int lt,
                             int fft_grid, cudaStream_t s);
 struct LargeAdjFftArgs;
 struct LargeInterpArgs;
@@ -104,6 +104,10 @@ struct TuneEnv {
     int q_median;             // the plan's median cell size
 };
 cudaError_t autotune_run(const TuneEnv& env, enufft_tuning* out);
+// synthetic samples of ncells cells (counts from offsets, written at offset - p0), uniform over each
+// cell's window: the tile tuning of the large route
+cudaError_t large_tune_samples(const CellConst* cells, const int64_t* offsets, int64_t p0, int ncells, float* x,
+                               float* y, float* h, float* w, cudaStream_t s);
 bool tune_cache_get(const char* path, const std::string& key, enufft_tuning* out);
 bool tune_cache_put(const char* path, const std::string& key, const enufft_tuning& t);
 

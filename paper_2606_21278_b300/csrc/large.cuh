@@ -1,15 +1,15 @@
 // large.cuh -- the type-1 transform for fine grids too large for one block's shared memory
 // (n_f = 256, P up to 128): a sorted-by-subgrid pipeline over batches of cells.
 //
-//   1. sort     per block of up to 4096 consecutive samples of one cell: the 32 x 32 tile of the
-//               fine grid holding each sample's centre node, a counting sort by tile inside the
-//               block's own range of the record buffer (16-byte records {x, y, h, w}), the 65 tile
+//   1. sort     per block of up to 4096 consecutive samples of one cell: the LT x LT tile of the
+//               fine grid holding each sample's centre node (LT = 16, 32 or 64, chosen per plan), a counting sort by tile inside the
+//               block's own range of the record buffer (16-byte records {x, y, h, w}), the tile
 //               offsets of the block and its per-tile sums of |w h| / |D|;
 //   2. scale    one warp per cell: the bound B of its fine grid's nodes and the grid's scale 2^k;
 //   3. spread   one block per (work item, tile), a work item being a cell or, for cells of more than
 //               2^18 samples, an interleaved part of its sort blocks (work items largest cell first):
 //               S = the sum of the item's sort blocks' per-tile sums bounds every node of its tile; each
-//               warp takes the tile's segment of one sort block at a time and spreads its records into a shared (32 + 2 halo)^2 tile in 32-bit fixed
+//               warp takes the tile's segment of one sort block at a time and spreads its records into a shared (LT + 2 halo)^2 tile in 32-bit fixed
 //               point at the item's own scale 2^30 (1 - 2^-8) / S; the tile is then added to the
 //               cell's fine grid in global memory (periodic wrap) in 64-bit fixed point at one scale
 //               per cell, 2^k with 2^61 / 2^k >= sum of the cell's per-tile sums (a bound of every
@@ -34,26 +34,28 @@ namespace enufft {
 
 // tile of a sample from a plain binary32 evaluation of its grid coordinate (only used to sort:
 // the exact coordinates are recomputed in step 4, and the tile halo absorbs a one-node difference)
+template <int LT>
 __device__ __forceinline__ int large_tile_of(const CellConst& cc, float px, float py) {
     const float sx = (px - cc.cxh) * cc.sch + 0.5f * kLNF, sy = (py - cc.cyh) * cc.sch + 0.5f * kLNF;
-    int tx = (int)floorf(sx) / kLT, ty = (int)floorf(sy) / kLT;
-    tx = tx < 0 ? 0 : (tx > kLNF / kLT - 1 ? kLNF / kLT - 1 : tx);
-    ty = ty < 0 ? 0 : (ty > kLNF / kLT - 1 ? kLNF / kLT - 1 : ty);
+    int tx = (int)floorf(sx) / LT, ty = (int)floorf(sy) / LT;
+    tx = tx < 0 ? 0 : (tx > kLNF / LT - 1 ? kLNF / LT - 1 : tx);
+    ty = ty < 0 ? 0 : (ty > kLNF / LT - 1 ? kLNF / LT - 1 : ty);
     if (!(sx == sx) || !(sy == sy)) { tx = 0; ty = 0; }
-    return ty * (kLNF / kLT) + tx;
+    return ty * (kLNF / LT) + tx;
 }
 
 // 1. counting sort of one block's samples by tile (per-warp histograms, then a tile-major,
 // warp-minor prefix), records written inside the block's own range
-static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_constant__ LargeArgs a) {
-    constexpr int NT = kLSortThreads, PER = kLBinBlock / NT, NW = NT / 32;
-    __shared__ int hist[NW][kLTiles];
-    __shared__ int toff[kLTiles + 1];
+template <int LT>
+__global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_constant__ LargeArgs a) {
+    constexpr int NT = kLSortThreads, PER = kLBinBlock / NT, NW = NT / 32, TT = large_tiles(LT);
+    __shared__ int hist[NW][TT];
+    __shared__ int toff[TT + 1];
     __shared__ float cabs[kLBinBlock];   // |w h| / |D| in sorted order
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int4 blk = a.blocks[blockIdx.x];
     const CellConst& cc = a.cells[a.cell0 + blk.x];
-    for (int i = tid; i < NW * kLTiles; i += NT) (&hist[0][0])[i] = 0;
+    for (int i = tid; i < NW * TT; i += NT) (&hist[0][0])[i] = 0;
     __syncthreads();
     float4 s[PER];
     int tl[PER], rk[PER];
@@ -69,12 +71,12 @@ static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const 
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         if (blk.y + tid + NT * i < blk.z) {
-            tl[i] = large_tile_of(cc, s[i].x, s[i].y);
+            tl[i] = large_tile_of<LT>(cc, s[i].x, s[i].y);
             rk[i] = atomicAdd(&hist[warp][tl[i]], 1);
         }
     }
     __syncthreads();
-    if (tid < kLTiles) {   // per tile: warp bases, then the tile's count
+    if (tid < TT) {   // per tile: warp bases, then the tile's count
         int run = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
@@ -85,23 +87,37 @@ static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const 
         toff[tid] = run;
     }
     __syncthreads();
-    if (warp == 0) {       // exclusive scan of the 64 tile counts (two per lane)
-        const int c0 = toff[2 * lane], c1 = toff[2 * lane + 1];
-        int v = c0 + c1;
+    if (warp == 0) {       // exclusive scan of the tile counts, PL per lane
+        constexpr int PL = TT >= 32 ? TT / 32 : 1;
+        int c[PL], sum = 0;
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+            const int tt = PL * lane + i;
+            c[i] = tt < TT ? toff[tt] : 0;
+            sum += c[i];
+        }
+        int v = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += u;
         }
-        const int e0 = v - c0 - c1;
+        int run = v - sum;
         __syncwarp();
-        toff[2 * lane] = e0;
-        toff[2 * lane + 1] = e0 + c0;
-        if (lane == 31) toff[kLTiles] = v;
-        int* bo = a.blk_off + (size_t)blockIdx.x * (kLTiles + 1);
-        bo[2 * lane] = e0;
-        bo[2 * lane + 1] = e0 + c0;
-        if (lane == 31) bo[kLTiles] = v;
+        int* bo = a.blk_off + (size_t)blockIdx.x * (TT + 1);
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+            const int tt = PL * lane + i;
+            if (tt < TT) {
+                toff[tt] = run;
+                bo[tt] = run;
+            }
+            run += c[i];
+        }
+        if (lane == 31) {
+            toff[TT] = v;
+            bo[TT] = v;
+        }
     }
     __syncthreads();
     const float inv_area = cc.inv_area;
@@ -114,50 +130,51 @@ static __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const 
             cabs[slot] = (v <= 3.0e38f) ? v : 0.0f;
         }
     __syncthreads();
-    {   // per-tile sums over the tile's contiguous slots, eight threads per tile
-        static_assert(NT == 8 * kLTiles, "eight threads per tile");
-        const int t = tid >> 3, sub = tid & 7;
+    // per-tile sums over the tile's contiguous slots, eight threads per tile
+    for (int t0 = 0; t0 < TT; t0 += NT / 8) {
+        const int t = t0 + (tid >> 3), sub = tid & 7;
         float sum = 0.0f;
-        for (int i = toff[t] + sub; i < toff[t + 1]; i += 8) sum += cabs[i];
+        if (t < TT)
+            for (int i = toff[t] + sub; i < toff[t + 1]; i += 8) sum += cabs[i];
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
         sum += __shfl_xor_sync(0xffffffffu, sum, 2);
         sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-        if (sub == 0) a.blk_abs[(size_t)blockIdx.x * kLTiles + t] = sum;
+        if (sub == 0 && t < TT) a.blk_abs[(size_t)blockIdx.x * TT + t] = sum;
     }
 }
 
 // 3. spread one (cell, tile): fixed point in shared memory, then added to the global fine grid
-template <int W>
+template <int W, int LT>
 struct LargeTileCfg {
     static constexpr int HS = W / 2 + 2;                   // halo per side
-    static constexpr int TS = kLT + 2 * HS;                // tile rows / columns used
+    static constexpr int TS = LT + 2 * HS;                // tile rows / columns used
     static constexpr int TSTR = TS | 1;                    // odd row stride
 };
 
-template <int W, int J = 0, int I = 0>
+template <int W, int LT, int J = 0, int I = 0>
 __device__ __forceinline__ void tile_taps(unsigned addr, const float (&kx)[W], const float (&ky)[W], float c) {
-    constexpr int S = LargeTileCfg<W>::TSTR;
+    constexpr int S = LargeTileCfg<W, LT>::TSTR;
     if constexpr (J < W) {
         if constexpr (I < W) {
             red_smem<J * S + I>(addr, __float2int_rn((c * ky[J]) * kx[I]));
-            tile_taps<W, J, I + 1>(addr, kx, ky, c);
+            tile_taps<W, LT, J, I + 1>(addr, kx, ky, c);
         } else {
-            tile_taps<W, J + 1, 0>(addr, kx, ky, c);
+            tile_taps<W, LT, J + 1, 0>(addr, kx, ky, c);
         }
     }
 }
 
-template <int W>
+template <int W, int LT>
 __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_spread_kernel(const __grid_constant__ LargeArgs a) {
-    using TC = LargeTileCfg<W>;
-    constexpr int NT = kLSpreadThreads, NW = NT / 32;
+    using TC = LargeTileCfg<W, LT>;
+    constexpr int NT = kLSpreadThreads, NW = NT / 32, TT = large_tiles(LT);
     __shared__ int tile[TC::TS * TC::TSTR];
     __shared__ CellConst scc;
     __shared__ float fsum[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int4 wk = a.work[blockIdx.x / kLTiles];
-    const int cl = wk.x, t = blockIdx.x % kLTiles, cell = a.cell0 + cl;
-    const int tx0 = (t % (kLNF / kLT)) * kLT - TC::HS, ty0 = (t / (kLNF / kLT)) * kLT - TC::HS;
+    const int4 wk = a.work[blockIdx.x / TT];
+    const int cl = wk.x, t = blockIdx.x % TT, cell = a.cell0 + cl;
+    const int tx0 = (t % (kLNF / LT)) * LT - TC::HS, ty0 = (t / (kLNF / LT)) * LT - TC::HS;
     {
         const int4* src = reinterpret_cast<const int4*>(a.cells + cell);
         int4* dst = reinterpret_cast<int4*>(&scc);
@@ -168,7 +185,7 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
     // S: the sum of this part's sort blocks' sums for this tile (fixed order per thread, then the
     // warps) bounds every node of the part's tile
     float s = 0.0f;
-    for (int j = wk.y + wk.z * tid; j < cb.y; j += wk.z * NT) s += a.blk_abs[(size_t)(cb.x + j) * kLTiles + t];
+    for (int j = wk.y + wk.z * tid; j < cb.y; j += wk.z * NT) s += a.blk_abs[(size_t)(cb.x + j) * TT + t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) fsum[warp] = s;
@@ -184,7 +201,7 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
     // mod parts); the next record is loaded before the current one is spread
     for (int j = wk.y + wk.z * warp; j < cb.y; j += wk.z * NW) {
         const int b = cb.x + j;
-        const int* bo = a.blk_off + (size_t)b * (kLTiles + 1);
+        const int* bo = a.blk_off + (size_t)b * (TT + 1);
         const int base = a.blocks[b].y;
         const int r1 = base + bo[t + 1];
         int r = base + bo[t] + lane;
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
                     if (lx < 0 || ly < 0 || lx > TC::TS - W || ly > TC::TS - W)
                         atomicOr(a.status, ST_BADCELL);   // cannot happen for samples sorted by this cell's frame
                     else
-                        tile_taps<W>(taddr + 4u * (unsigned)(ly * TC::TSTR + lx), kx, ky, c);
+                        tile_taps<W, LT>(taddr + 4u * (unsigned)(ly * TC::TSTR + lx), kx, ky, c);
                 }
             }
             cur = nxt;
@@ -227,13 +244,15 @@ __global__ void __launch_bounds__(kLSpreadThreads, ENUFFT_LSPREAD_MINB) large_sp
 // and k = 61 - e for B < 2^e, so the grid's integers stay below 2^61 (B is accurate to far better
 // than the factor 2 left to 2^62); one warp per cell
 constexpr int kLScaleThreads = 256;
-static __global__ void __launch_bounds__(kLScaleThreads) large_scale_kernel(const __grid_constant__ LargeArgs a) {
+template <int LT>
+__global__ void __launch_bounds__(kLScaleThreads) large_scale_kernel(const __grid_constant__ LargeArgs a) {
+    constexpr int TT = large_tiles(LT);
     const int lane = threadIdx.x & 31;
     const int cl = blockIdx.x * (kLScaleThreads / 32) + (threadIdx.x >> 5);
     if (cl >= a.ncells) return;
     const int2 cb = a.cell_blocks[cl];
     float s = 0.0f;
-    for (int i = lane; i < cb.y * kLTiles; i += 32) s += a.blk_abs[(size_t)cb.x * kLTiles + i];
+    for (int i = lane; i < cb.y * TT; i += 32) s += a.blk_abs[(size_t)cb.x * TT + i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {

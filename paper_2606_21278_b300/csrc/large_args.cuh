@@ -8,8 +8,9 @@ namespace enufft {
 
 constexpr int kMaxHalfL = 64;                 // P/2 <= 64
 constexpr int kLNF = 256;                     // fine grid
-constexpr int kLT = 32;                       // tile side (nodes)
-constexpr int kLTiles = (kLNF / kLT) * (kLNF / kLT);   // 64 tiles per cell
+constexpr int kLT = 32;                       // default tile side (nodes); 16 and 64 are built too
+__host__ __device__ constexpr int large_tiles(int lt) { return (kLNF / lt) * (kLNF / lt); }
+constexpr int kLTilesMax = large_tiles(16);   // tiles per cell at the smallest side (256)
 constexpr int kLBinBlock = 4096;              // samples per sort block (one cell's consecutive samples)
 constexpr int kLSortThreads = 512;
 constexpr int kLSpreadThreads = 256;
@@ -27,8 +28,8 @@ struct LargeArgs {
     const int4* __restrict__ blocks;          // sort blocks: {cell - cell0, q_begin - p0, q_end - p0, 0}
     const int2* __restrict__ cell_blocks;     // per batch cell: {first sort block (batch relative), count}
     const int4* __restrict__ work;            // spread work items, largest cells first: {cell - cell0, part, parts, 0}
-    int* blk_off;                             // [sort block][kLTiles + 1]: tile offsets inside the block's range
-    float* blk_abs;                           // [sort block][kLTiles]: sum |w h| / |D| of the block's samples per tile
+    int* blk_off;                             // [sort block][tiles + 1]: tile offsets inside the block's range
+    float* blk_abs;                           // [sort block][tiles]: sum |w h| / |D| of the block's samples per tile
     float4* rec;                              // [batch points] records {x, y, h, w}, tile-ordered per sort block
     unsigned long long* grid;                 // [ncells][256][256] fine grids, 64-bit two's complement
                                               // fixed point at the cell's scale 2^k (cell_exp)

@@ -116,7 +116,7 @@ def test_tune_cache_round_trip(tmp_path, lib):
     import json
     path = str(tmp_path / "tune.json")
     a = {"tc_max_points": 512, "fused_blocks_per_sm": 2, "ladder": [128, 256, 512, 1024],
-         "ns_fused": [0.31, 0.16, 0.09, 0.05], "ns_tc": [0.2, 0.15, 0.08, 0.07]}
+         "ns_fused": [0.31, 0.16, 0.09, 0.05], "ns_tc": [0.2, 0.15, 0.08, 0.07], "large_tile": 64}
     b = {"tc_max_points": 0, "fused_blocks_per_sm": 1, "ladder": [], "ns_fused": [], "ns_tc": []}
     assert enufft.tune_cache_lookup(path, "k1") is None                       # no file yet
     enufft.tune_cache_store(path, "gpu=X|P=64", a)
@@ -124,7 +124,7 @@ def test_tune_cache_round_trip(tmp_path, lib):
     got = enufft.tune_cache_lookup(path, "gpu=X|P=64")
     assert got["tc_max_points"] == 512 and got["fused_blocks_per_sm"] == 2 and got["ladder"] == a["ladder"]
     assert got["ns_fused"] == pytest.approx(a["ns_fused"], rel=1e-5) and got["ns_tc"] == pytest.approx(a["ns_tc"], rel=1e-5)
-    assert got["from_cache"] is True
+    assert got["from_cache"] is True and got["large_tile"] == 64
     assert enufft.tune_cache_lookup(path, "gpu=X|P=32")["tc_max_points"] == 0
     assert enufft.tune_cache_lookup(path, "gpu=Y|P=64") is None
     enufft.tune_cache_store(path, "gpu=X|P=64", {**a, "tc_max_points": 1024})  # replaced, not duplicated
@@ -133,7 +133,11 @@ def test_tune_cache_round_trip(tmp_path, lib):
     open(path, "w").write("{not json")
     assert enufft.tune_cache_lookup(path, "gpu=X|P=64") is None
     enufft.tune_cache_store(path, "k", b)
-    assert json.load(open(path)) == {"k": {"tc_max_points": 0, "fused_blocks_per_sm": 1, "ladder": [],
-                                           "ns_fused": [], "ns_tc": []}}
+    assert json.load(open(path)) == {"k": {"tc_max_points": 0, "fused_blocks_per_sm": 1, "large_tile": 0,
+                                           "ladder": [], "ns_fused": [], "ns_tc": []}}
+    # records written before the tile field existed read as large_tile 0
+    open(path, "w").write('{"old": {"tc_max_points": 0, "fused_blocks_per_sm": 1, "ladder": [], "ns_fused": [], '
+                          '"ns_tc": []}}')
+    assert enufft.tune_cache_lookup(path, "old")["large_tile"] == 0
     with pytest.raises(enufft.EnufftError):
         enufft.tune_cache_store(path, 'bad"key', b)

@@ -1,7 +1,10 @@
 """Route tuning at plan creation (opts.autotune, enufft_get_tuning): the tuned plan reports a threshold
 taken from the measured ladder and a fused-kernel grid, gives the oracle's coefficients and EMS
 selection on whichever route each cell took, and a second plan with the same cache file reads the
-record instead of measuring."""
+record instead of measuring.  For n_f = 256 plans the tuner picks the tile side of the sorted
+spreading, and every side gives the oracle's result."""
+import json
+
 import numpy as np
 import pytest
 
@@ -48,3 +51,40 @@ def test_autotune_without_tensor_core_cap_tunes_the_grid_only():
     t = plan.tuning()
     assert t["ladder"] == [] and t["tc_max_points"] == 0 and plan.info()["cells_tensor"] == 0
     assert plan.info()["fused_blocks_per_sm"] == t["fused_blocks_per_sm"]
+
+
+def _large_workload():
+    # n_f = 256 cells (P = 128) of about 1,200 to 20,000 samples: several sort blocks per cell
+    return synth.make("mixed2560_p128", seed=6, n_cells=6, q_scale=0.012)
+
+
+def test_large_route_tile_tuning_and_every_tile_side_matches_oracle(tmp_path):
+    cache = str(tmp_path / "tune.json")
+    wl = _large_workload()
+    g = wl.to("cuda")
+    plan = enufft.Plan.for_workload(g, autotune=True, tune_cache=cache)
+    info, t = plan.info(), plan.tuning()
+    assert info["cells_large"] == wl.n_cells and info["autotuned"] == 1 and not t["from_cache"]
+    assert t["ladder"] == [16, 32, 64] and all(v > 0 for v in t["ns_fused"])
+    assert t["large_tile"] == t["ladder"][int(np.argmin(t["ns_fused"]))] == info["large_tile"]
+    ref = oracle.type1(wl)
+    (key,) = json.load(open(cache)).keys()
+    for side in (16, 32, 64):   # each side through the cache record
+        d = json.load(open(cache))
+        d[key]["large_tile"] = side
+        json.dump(d, open(cache, "w"))
+        p2 = enufft.Plan.for_workload(g, autotune=True, tune_cache=cache)
+        assert p2.tuning()["from_cache"] and p2.info()["large_tile"] == side
+        c, ks, sel, _ = p2.type1_ems(g.x, g.y, g.h, g.w)
+        p2.sync_status()
+        cn = c.cpu().numpy()
+        err = np.linalg.norm((cn - ref).reshape(wl.n_cells, -1), axis=1) / np.linalg.norm(ref.reshape(wl.n_cells, -1), axis=1)
+        assert err.max() <= 1e-5, (side, err)
+        oks, osel, _, _ = oracle.ems(cn, OEMS(), energy_fp32=True)
+        assert np.array_equal(ks.cpu().numpy(), oks) and np.array_equal(sel.cpu().numpy(), osel)
+
+
+def test_large_route_default_tile_without_tuning():
+    g = _large_workload().to("cuda")
+    plan = enufft.Plan.for_workload(g)
+    assert plan.info()["large_tile"] == 32 and plan.info()["autotuned"] == 0
