@@ -3,15 +3,17 @@
 //
 //   h^[n][m] = (1/|D|) sum_q win_q w_q h_q e^{-i k_n y'_q} e^{-i k_m x'_q},   k = 2 pi / L,
 //
-// i.e. D = A^T B with A[q][.] = c_q (e^{-i k_n y'_q})_n over n in [-P/2, P/2) and
-// B[q][.] = (e^{-i k_m' x'_q})_m' over m' in [0, P/2] only: the samples are real, so the phasor of
-// -m' is the conjugate of that of m', and with P1 = D[re n][re m'], P2 = D[im n][im m'],
-// P3 = D[im n][re m'], P4 = D[re n][im m']
-//   h^[n][ m'] = (P1 - P2) + i (P3 + P4),   h^[n][-m'] = (P1 + P2) + i (P3 - P4).
-// Complex values are stacked as real features: A has 128 (the real and imaginary parts of 16
-// consecutive modes n alternate in blocks of 16, so both sit in one 32-lane quarter of the
-// accumulator), B has 80 (likewise for m' = 0..31, then the real and imaginary parts of m' = 32),
-// so one 128 x 80 real product per 16 samples carries the whole P x P complex result (P <= 64).
+// i.e. D = A^T B with A[q][.] = c_q (e^{-i k_n y'_q})_n and B[q][.] = (e^{-i k_m' x'_q})_m'.  The
+// samples are real, so the spectrum is Hermitian, h^(-m, -n) = conj h^(m, n), and the phasor of -m'
+// is the conjugate of that of m': A carries only n = 0 .. P/2 and B only m' = 0 .. P/2.  With
+// P1 = D[re n][re m'], P2 = D[im n][im m'], P3 = D[im n][re m'], P4 = D[re n][im m']
+//   h^[n][ m'] = (P1 - P2) + i (P3 + P4),   h^[n][-m'] = (P1 + P2) + i (P3 - P4),
+// and the rows n < 0 are the conjugates of these.  Complex values are stacked as real features:
+// A has 128 (the real and imaginary parts of n = 1 .. 32 alternate in blocks of 16, so both sit in
+// one 32-lane quarter of the accumulator; the real weight of n = 0 at feature 64; features 65 ..
+// 127 carry whatever the buffer holds and their accumulator rows are never read), B has 80
+// (likewise for m' = 0 .. 31, then the real and imaginary parts of m' = 32), so one 128 x 80 real
+// product per 16 samples carries the whole P x P complex result (P <= 64).
 // Each value is split into binary16 hi + lo and the product is accumulated in binary32 as
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo * lo term is below 2^-22 of the scale).  The samples'
 // weights are scaled by 1 / max |c| of the cell so that every operand lies in [-1, 1].
@@ -28,10 +30,10 @@
 // other chunk of samples (window, scaled weight, coordinates, unit phasor steps) into a ring of four
 // set-up buffers, with the samples of their next chunk already loaded; one warp issues the tcgen05
 // MMAs; eight operand warps turn each chunk of 32 samples into binary16 operands in shared memory
-// (four stages).  The hand-offs are mbarriers with bounded waits (set-up ready, set-up read,
-// operands written, MMAs done), so
-// the operand warps never wait on a block-wide barrier inside a cell.  The spectrum is written out
-// and ranked for EMS (Sec. 2.2).
+// (four stages), warps 0-3 the B octets and warps 4-7 the A octets, one task per thread.  The
+// hand-offs are mbarriers with bounded waits (set-up ready, set-up read, operands written, MMAs
+// done), so the operand warps never wait on a block-wide barrier inside a cell.  The spectrum is
+// written out and ranked for EMS (Sec. 2.2).
 #include <cuda_fp16.h>
 
 #include "ems.cuh"
@@ -48,7 +50,7 @@ constexpr int kMmaWarp = kFeatThreads / 32;               // warp 8: MMA issue
 constexpr int kPrepWarp0 = kMmaWarp + 1;                  // warps 9, 10: sample set-up of stage 0, 1
 constexpr int kTcThreads = kFeatThreads + 3 * 32;
 constexpr int kCh = 32;                                   // samples per chunk (K of one stage)
-constexpr int kFeatA = 128, kFeatB = 80;                  // stacked features of A (n) and B (m' >= 0)
+constexpr int kFeatA = 128, kFeatB = 80;                  // stacked features of A (n >= 0) and B (m' >= 0)
 using LayA = tc::OpLayout<kFeatA>;
 using LayB = tc::OpLayout<kFeatB>;
 constexpr unsigned kOpA = kCh * kFeatA * 2;               // one A operand (8 KB)
@@ -77,8 +79,10 @@ static_assert(kStageBytes % 16 == 0 && kOpA % 16 == 0 && kOpB % 16 == 0, "descri
 static_assert(kFeatThreads == 8 * kCh, "one (sample, feature octet) task per operand thread and axis");
 static_assert(144 + 4 * (kTcThreads / 32) <= 192, "barriers, TMEM base and warp maxima fit the misc area");
 
-// feature of the real part of the first mode of octet o (modes 8 o .. 8 o + 7 of A, or of B for
-// o < 4): blocks of 16 real parts followed by their 16 imaginary parts; the imaginary part of a
+constexpr int kFeatN0 = 64;   // A feature of the mode n = 0 (features 65 .. 127 of A are never read)
+
+// feature of the real part of the first mode of octet o (modes 8 o + 1 .. 8 o + 8 of A, 8 o .. 8 o + 7
+// of B, o < 4): blocks of 16 real parts followed by their 16 imaginary parts; the imaginary part of a
 // mode is 16 features later, except in B's last octet (m' = 32 .. 39: real 64.., imaginary 72..)
 __host__ __device__ constexpr int feat_re(int o) { return 32 * (o >> 1) + 8 * (o & 1); }
 __host__ __device__ constexpr int feat_im_b(int o) { return o == 4 ? 72 : feat_re(o) + 16; }
@@ -224,11 +228,13 @@ __device__ __forceinline__ void tc_accumulate(unsigned tmem, unsigned bank, int 
 }
 
 // The cell's spectrum from the running total, scaled by `scale`, into hs (every entry written by
-// one operand thread).  Warp w reads lane quarter w & 3, i.e. A features 32 (w & 3) + l: the real
-// (l < 16) or imaginary (l >= 16) part of n-slot 16 (w & 3) + (l & 15), and the B modes
-// m' = 16 (w >> 2) .. + 15 (plus m' = 32 for w >> 2 == 1).  Lanes l and l ^ 16 exchange their
-// products; lane l < 16 writes the entries (m', n), lane l >= 16 the entries (-m', n).  A cell
-// without chunks (`empty`) gets zeros.
+// one operand thread).  Warp w reads lane quarter w & 3 and the B modes m' = 16 (w >> 2) .. + 15
+// (plus m' = 32 for w >> 2 == 1).  Quarters 0 and 1 hold the A features 32 q + l: the real (l < 16)
+// or imaginary (l >= 16) part of the mode n = 16 q + (l & 15) + 1; lanes l and l ^ 16 exchange
+// their products, lane l < 16 forms h^(m', n) and lane l >= 16 h^(-m', n), and each also writes
+// the conjugate at (-m, -n) (the samples are real).  Quarter 2's lane 0 holds n = 0 (real weight
+// only): its lanes 0 and 16 form h^(m', 0) and h^(-m', 0).  A cell without chunks (`empty`) gets
+// zeros.
 __device__ __forceinline__ void tc_combine(unsigned tmem, cplx<float>* hs, int warp, int lane, int P, float scale,
                                            bool empty) {
     const int lq = warp & 3, hh = warp >> 2, half = P / 2;
@@ -248,23 +254,58 @@ __device__ __forceinline__ void tc_combine(unsigned tmem, cplx<float>* hs, int w
         for (int j = 0; j < 16; ++j) vr[j] = vi[j] = 0.0f;
     }
     const bool up = lane < 16;
-    const int ns = 16 * lq + (lane & 15);   // n-slot (n = ns - P/2)
-    cplx<float>* row = hs + ns * kHS;
-    const bool nrow = ns < P;
+    const bool zrow = lq == 2;                            // n = 0 (lanes 0 and 16 only)
+    const int n = zrow ? 0 : 16 * lq + (lane & 15) + 1;
+    const bool live = lq < 2 ? n <= half : (zrow && (lane & 15) == 0);
+    cplx<float>* row = hs + (n + half) * kHS;             // row n (direct entries, n <= half - 1)
+    cplx<float>* crow = hs + (half - n) * kHS;            // row -n (conjugates)
+    const bool direct = live && n <= half - 1;
+    const bool conj = live && !zrow;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         const float pr = __shfl_xor_sync(0xffffffffu, vr[j], 16), pi = __shfl_xor_sync(0xffffffffu, vi[j], 16);
         const int mp = 16 * hh + j;
         // lane < 16: vr = P1, vi = P4, pr = P3, pi = P2;  lane >= 16: vr = P3, vi = P2, pr = P1, pi = P4
-        const bool ok = nrow && (up ? mp < half : (mp >= 1 && mp <= half));
-        const int col = up ? half + mp : half - mp;
-        const float re = up ? vr[j] - pi : pr + vi[j];
-        const float im = up ? pr + vi[j] : vr[j] - pi;
-        if (ok) row[col] = cplx<float>{re * scale, im * scale};
+        // (row n = 0: P2 = P3 = 0, the lane-16 values unused)
+        float re, im;
+        if (zrow) {
+            re = up ? vr[j] : pr;
+            im = up ? vi[j] : -pi;
+        } else {
+            re = up ? vr[j] - pi : pr + vi[j];
+            im = up ? pr + vi[j] : vr[j] - pi;
+        }
+        re *= scale;
+        im *= scale;
+        if (up) {   // (m', n), m' <= half - 1; conjugate at (-m', -n), m' <= half
+            if (direct && mp <= half - 1) row[half + mp] = cplx<float>{re, im};
+            if (conj && mp <= half) crow[half - mp] = cplx<float>{re, -im};
+        } else {    // (-m', n), 1 <= m' <= half; conjugate at (m', -n) for m' <= half - 1
+            if (mp >= 1 && mp <= half) {
+                if (direct) row[half - mp] = cplx<float>{re, im};
+                if (conj && mp <= half - 1) crow[half + mp] = cplx<float>{re, -im};
+            }
+        }
     }
-    const float pr = __shfl_xor_sync(0xffffffffu, xr, 16), pi = __shfl_xor_sync(0xffffffffu, xi, 16);
-    if (hh == 1 && !up && nrow && half == 32)   // (-32, n): P1 + P2, P3 - P4
-        row[0] = cplx<float>{(pr + xi) * scale, (xr - pi) * scale};
+    if (hh == 1 && half == 32) {   // m' = 32: (-32, n) from the lane >= 16 side, (32, n) only as the
+                                   // conjugate (-32, -n) from the lane < 16 side
+        const float pr = __shfl_xor_sync(0xffffffffu, xr, 16), pi = __shfl_xor_sync(0xffffffffu, xi, 16);
+        float re, im;
+        if (zrow) {
+            re = up ? xr : pr;
+            im = up ? xi : -pi;
+        } else {
+            re = up ? xr - pi : pr + xi;
+            im = up ? pr + xi : xr - pi;
+        }
+        re *= scale;
+        im *= scale;
+        if (up) {
+            if (conj) crow[0] = cplx<float>{re, -im};
+        } else {
+            if (direct) row[0] = cplx<float>{re, im};
+        }
+    }
 }
 
 template <bool FULL>
@@ -413,33 +454,46 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_nudft_kernel(const __grid_co
                 if (!tc::mbar_wait(tc::smem_addr(&bar_prep[b]), (gc / kPrepBufs) & 1u, kWaitLimit))
                     atomicOr(a.status, ST_TIMEOUT);
                 const float* pr = prep + b * kPrepF * kCh;
-                const float ca = pr[k], tya = pr[3 * kCh + k], tyl = pr[4 * kCh + k], wya = pr[7 * kCh + k],
-                            wyi = pr[8 * kCh + k];
-                float txa = 0.f, txl = 0.f, wxa = 0.f, wxi = 0.f;
+                // warps 0-3 take the B octets (x), warps 4-7 the A octets (y): one task per thread
+                float ta, tl, wa, wi, ca = 0.f;
                 if (warp < 4) {
-                    txa = pr[1 * kCh + k];
-                    txl = pr[2 * kCh + k];
-                    wxa = pr[5 * kCh + k];
-                    wxi = pr[6 * kCh + k];
+                    ta = pr[1 * kCh + k];
+                    tl = pr[2 * kCh + k];
+                    wa = pr[5 * kCh + k];
+                    wi = pr[6 * kCh + k];
+                } else {
+                    ca = pr[k];
+                    ta = pr[3 * kCh + k];
+                    tl = pr[4 * kCh + k];
+                    wa = pr[7 * kCh + k];
+                    wi = pr[8 * kCh + k];
                 }
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar_pfree[b]));
                 unsigned char* stg = smem + st * kStageBytes;
-                {   // A: modes n = 8 o - P/2 .. + 7 (y), times the scaled weight
+                if (warp >= 4) {   // A: modes n = 8 o' + 1 .. 8 o' + 8 (y) times the scaled weight, o' = o - 4
+                    const int oa = o - 4;
                     float re[8], im[8], r8, i8;
-                    tc_phasors<FULL>(tya, tyl, wya, wyi, ca, 8 * o - half, 8 * o, P, re, im, r8, i8);
+                    tc_phasors<FULL>(ta, tl, wa, wi, ca, 8 * oa + 1, 8 * oa, half, re, im, r8, i8);
                     uint4 rh, rl, ih, il;
                     tc_split8(re, rh, rl);
                     tc_split8(im, ih, il);
-                    const unsigned fr = LayA::off(feat_re(o), k), fi = LayA::off(feat_re(o) + 16, k);
+                    const unsigned fr = LayA::off(feat_re(oa), k), fi = LayA::off(feat_re(oa) + 16, k);
                     *reinterpret_cast<uint4*>(stg + fr) = rh;
                     *reinterpret_cast<uint4*>(stg + kOpA + fr) = rl;
                     *reinterpret_cast<uint4*>(stg + fi) = ih;
                     *reinterpret_cast<uint4*>(stg + kOpA + fi) = il;
+                    if (oa == 0) {   // n = 0: the real weight alone, at feature kFeatN0
+                        const __half chh = __float2half_rn(ca);
+                        const __half chl = __float2half_rn(ca - __half2float(chh));
+                        const unsigned f0 = LayA::off(kFeatN0, k);
+                        *reinterpret_cast<uint4*>(stg + f0) = make_uint4(__half_as_ushort(chh), 0u, 0u, 0u);
+                        *reinterpret_cast<uint4*>(stg + kOpA + f0) = make_uint4(__half_as_ushort(chl), 0u, 0u, 0u);
+                    }
                 }
                 if (warp < 4) {   // B: modes m' = 8 o .. 8 o + 7 (x), o < 4; octet 3 also writes m' = 32 .. 39
                     float re[8], im[8], r8, i8;
-                    tc_phasors<FULL>(txa, txl, wxa, wxi, 1.0f, 8 * o, 8 * o, half + 1, re, im, r8, i8);
+                    tc_phasors<FULL>(ta, tl, wa, wi, 1.0f, 8 * o, 8 * o, half + 1, re, im, r8, i8);
                     uint4 rh, rl, ih, il;
                     tc_split8(re, rh, rl);
                     tc_split8(im, ih, il);
