@@ -252,6 +252,11 @@ class Plan:
         self._check(self._lib.enufft_type1(self._h, _ptr(x), _ptr(y), _ptr(h), _ptr(w), _ptr(coeffs)), "type1")
         return coeffs
 
+    def new_ems_out(self, params: EMSParams = EMSParams()):
+        """Preallocated EMS outputs (kstar, sel, retained) for `type1_ems(out=...)` and
+        `type1_ems_graph`."""
+        return self._ems_out(params)
+
     def _ems_out(self, params: EMSParams):
         dev = self.offsets.device
         return (torch.empty(self.n_cells, dtype=torch.int32, device=dev),
