@@ -117,30 +117,28 @@ __device__ __forceinline__ bool window_f64(const CellConst& cc, double x, double
     return true;
 }
 
-// binary32 window test with a certified margin: returns 1 inside, 0 outside, -1 undecided
+// binary32 window test with a certified margin: returns 1 inside, 0 outside, -1 undecided.  The
+// window is the intersection of half-planes (the square B, and the cell's edges or the disk), so the
+// test takes the largest excess over the constraints: outside where it exceeds the margin, inside
+// where it is below minus the margin, undecided in between.  One multiply-add pair and one maximum
+// per edge, over the cell's own edge count (coordinates are finite: callers test that first).
 __device__ __forceinline__ int window_f32(const FastFrame& ff, const float4* __restrict__ edge, float ux, float uy) {
     const float tau = ff.tau;
-    int unsure = 0;
-    const float bx = fabsf(ux) - ff.Hf, by = fabsf(uy) - ff.Hf;
-    if (bx > tau || by > tau) return 0;
-    unsure |= (bx > -tau) | (by > -tau);
+    float f = fmaxf(fabsf(ux) - ff.Hf, fabsf(uy) - ff.Hf);
     if (ff.mask == 0) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            if (i < ff.nv) {
-                const float4 e = edge[i];
-                const float f = __fmaf_rn(e.x, ux, __fmaf_rn(e.y, uy, -e.z));
-                if (f > tau) return 0;
-                unsure |= f > -tau;
-            }
+#pragma unroll 1
+        for (int i = 0; i < ff.nv; ++i) {
+            const float4 e = edge[i];
+            f = fmaxf(f, __fmaf_rn(e.x, ux, __fmaf_rn(e.y, uy, -e.z)));
         }
-    } else if (ff.mask == 2) {
-        const float f = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, -ff.Hf * ff.Hf));
+    } else if (ff.mask == 2) {   // the disk's margin is 4 tau H on the squared radius
+        const float fc = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, -ff.Hf * ff.Hf));
         const float t2 = 4.0f * tau * ff.Hf;
-        if (f > t2) return 0;
-        unsure |= f > -t2;
+        if (fc > t2) return 0;
+        if (fc > -t2) f = fmaxf(f, 0.0f);   // undecided unless the square already excludes it
     }
-    return unsure ? -1 : 1;
+    if (f > tau) return 0;
+    return f > -tau ? -1 : 1;
 }
 
 // Horner evaluation of the W kernel pieces at u in [-1, 1] (DEG coefficients, compile time)
@@ -311,15 +309,17 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
     int par = 0;
     for (int64_t c0 = q0; c0 < q1; c0 += CH, par ^= 1) {
         int* hist = shist + 32 * par;
+        // samples c0 + tid + k NT of this chunk exist for k NT < nrem
+        const int nrem = (int)(q1 - c0 < (int64_t)CH ? q1 - c0 : (int64_t)CH) - tid;
+        const float *xc = x + c0 + tid, *yc = y + c0 + tid, *hc = h + c0 + tid, *wc = w + c0 + tid;
         float px[K], py[K], ph[K], pw[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int64_t q = c0 + tid + (int64_t)k * NT;
-            const bool in = q < q1;
-            px[k] = in ? x[q] : 0.0f;
-            py[k] = in ? y[q] : 0.0f;
-            ph[k] = in ? h[q] : 0.0f;
-            pw[k] = in ? w[q] : 0.0f;
+            const bool in = k * NT < nrem;
+            px[k] = in ? xc[k * NT] : 0.0f;
+            py[k] = in ? yc[k * NT] : 0.0f;
+            ph[k] = in ? hc[k * NT] : 0.0f;
+            pw[k] = in ? wc[k * NT] : 0.0f;
         }
         int4 rec[K];
         int cls[K], slot[K];
@@ -330,8 +330,7 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
             rec[k] = make_int4(0, 0, 0, 0);
             int r0x, r0y;
             float ax, ay;
-            if (c0 + tid + (int64_t)k * NT < q1 &&
-                prep_coords_f32<NF, W>(ff, edge, cc, px[k], py[k], r0x, r0y, ax, ay, status)) {
+            if (k * NT < nrem && prep_coords_f32<NF, W>(ff, edge, cc, px[k], py[k], r0x, r0y, ax, ay, status)) {
                 const float cs = pw[k] * ph[k] * ff.inv_area * scale;
                 if (!isfinite(cs)) {
                     atomicOr(status, ST_NONFINITE);
