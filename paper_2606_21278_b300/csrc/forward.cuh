@@ -156,10 +156,22 @@ __device__ __forceinline__ void kernel_pieces(const KernelPoly& kp, float u, flo
 // Per-sample setup shared by spreading and interpolation (binary32 path): window test, first
 // node r0 of each dimension and the W kernel values there.  Returns false for samples outside
 // the window (or non-finite ones, which also latch ST_NONFINITE).
-template <int NF, int W>
-__device__ __forceinline__ bool prep_coords_f32(const FastFrame& ff, const float4* __restrict__ edge,
-                                                const CellConst& cc, float px, float py, int& r0x, int& r0y,
-                                                float& argx, float& argy, unsigned* status) {
+// The three-edge case of window_f32 (triangular cells), the edges held in registers.
+__device__ __forceinline__ int window_tri_f32(const FastFrame& ff, const float4& e0, const float4& e1, const float4& e2,
+                                              float ux, float uy) {
+    float f = fmaxf(fabsf(ux) - ff.Hf, fabsf(uy) - ff.Hf);
+    f = fmaxf(f, __fmaf_rn(e0.x, ux, __fmaf_rn(e0.y, uy, -e0.z)));
+    f = fmaxf(f, __fmaf_rn(e1.x, ux, __fmaf_rn(e1.y, uy, -e1.z)));
+    f = fmaxf(f, __fmaf_rn(e2.x, ux, __fmaf_rn(e2.y, uy, -e2.z)));
+    if (f > ff.tau) return 0;
+    return f > -ff.tau ? -1 : 1;
+}
+
+// prep_coords_f32 with the binary32 window test given by the caller (win(ux, uy) as window_f32)
+template <int NF, int W, typename Win>
+__device__ __forceinline__ bool prep_coords_win_f32(const FastFrame& ff, const Win& win_f32, const CellConst& cc,
+                                                    float px, float py, int& r0x, int& r0y, float& argx, float& argy,
+                                                    unsigned* status) {
     if (!(isfinite(px) && isfinite(py))) {
         atomicOr(status, ST_NONFINITE);
         return false;
@@ -169,7 +181,7 @@ __device__ __forceinline__ bool prep_coords_f32(const FastFrame& ff, const float
     uxl = __fsub_rn(uxl, ff.cxl);
     two_diff(py, ff.cyh, uyh, uyl);
     uyl = __fsub_rn(uyl, ff.cyl);
-    int win = window_f32(ff, edge, uxh + uxl, uyh + uyl);
+    int win = win_f32(uxh + uxl, uyh + uyl);
     if (win < 0) win = window_f64(cc, (double)px, (double)py);
     if (!win) return false;
     // grid coordinate s = u * (n_f / L) + n_f / 2; first node r0 = ceil(s - W/2);
@@ -183,6 +195,14 @@ __device__ __forceinline__ bool prep_coords_f32(const FastFrame& ff, const float
     argx = __fmaf_rn(2.0f, tx, -1.0f);
     argy = __fmaf_rn(2.0f, ty, -1.0f);
     return true;
+}
+
+template <int NF, int W>
+__device__ __forceinline__ bool prep_coords_f32(const FastFrame& ff, const float4* __restrict__ edge,
+                                                const CellConst& cc, float px, float py, int& r0x, int& r0y,
+                                                float& argx, float& argy, unsigned* status) {
+    return prep_coords_win_f32<NF, W>(ff, [&](float ux, float uy) { return window_f32(ff, edge, ux, uy); }, cc, px, py,
+                                      r0x, r0y, argx, argy, status);
 }
 
 template <int NF, int W>
@@ -306,6 +326,8 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
                                                 int64_t q1, float scale, unsigned* status) {
     constexpr int K = kSpreadPerThread, CH = NT * K, NWARPS = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool tri = ff.mask == 0 && ff.nv == 3;
+    const float cscale = ff.inv_area * scale;
     int par = 0;
     for (int64_t c0 = q0; c0 < q1; c0 += CH, par ^= 1) {
         int* hist = shist + 32 * par;
@@ -323,24 +345,32 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
         }
         int4 rec[K];
         int cls[K], slot[K];
+        auto prep = [&](const auto& win) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            cls[k] = -1;
-            slot[k] = 0;
-            rec[k] = make_int4(0, 0, 0, 0);
-            int r0x, r0y;
-            float ax, ay;
-            if (k * NT < nrem && prep_coords_f32<NF, W>(ff, edge, cc, px[k], py[k], r0x, r0y, ax, ay, status)) {
-                const float cs = pw[k] * ph[k] * ff.inv_area * scale;
-                if (!isfinite(cs)) {
-                    atomicOr(status, ST_NONFINITE);
-                } else {
-                    const int word = (r0y + HO) * GS + (r0x + HO);
-                    cls[k] = word & 31;
-                    slot[k] = atomicAdd(&hist[cls[k]], 1);
-                    rec[k] = make_int4(word, __float_as_int(ax), __float_as_int(ay), __float_as_int(cs));
+            for (int k = 0; k < K; ++k) {
+                cls[k] = -1;
+                slot[k] = 0;
+                rec[k] = make_int4(0, 0, 0, 0);
+                int r0x, r0y;
+                float ax, ay;
+                if (k * NT < nrem && prep_coords_win_f32<NF, W>(ff, win, cc, px[k], py[k], r0x, r0y, ax, ay, status)) {
+                    const float cs = pw[k] * ph[k] * cscale;
+                    if (!isfinite(cs)) {
+                        atomicOr(status, ST_NONFINITE);
+                    } else {
+                        const int word = (r0y + HO) * GS + (r0x + HO);
+                        cls[k] = word & 31;
+                        slot[k] = atomicAdd(&hist[cls[k]], 1);
+                        rec[k] = make_int4(word, __float_as_int(ax), __float_as_int(ay), __float_as_int(cs));
+                    }
                 }
             }
+        };
+        if (tri) {   // triangles: the three edges in registers for the chunk
+            const float4 e0 = edge[0], e1 = edge[1], e2 = edge[2];
+            prep([&](float ux, float uy) { return window_tri_f32(ff, e0, e1, e2, ux, uy); });
+        } else {
+            prep([&](float ux, float uy) { return window_f32(ff, edge, ux, uy); });
         }
         __syncthreads();   // every slot taken; the previous chunk's records are spread
         if (warp == 0) shist[32 * (par ^ 1) + lane] = 0;   // the next chunk's counters
