@@ -185,17 +185,26 @@ __device__ __forceinline__ void tc_prep_sample(const FastFrame& ff, const CellCo
     pr[8 * kCh + k] = sy;
 }
 
+// two binary32 values -> binary16 hi = rn(v) and lo = rn(v - hi), packed in pairs (v0 in the low
+// halves).  v - hi is exact in binary32 and formed by one mixed-precision multiply-add per value
+// (hi * -1 + v, hi read as binary16), so there is no conversion of hi back to binary32.
+__device__ __forceinline__ void tc_split2(float v0, float v1, unsigned& hi, unsigned& lo) {
+    asm("{\n\t.reg .f16 h0, h1, m1;\n\t.reg .f32 r0, r1;\n\t"
+        "cvt.rn.f16x2.f32 %0, %3, %2;\n\t"
+        "mov.b32 {h0, h1}, %0;\n\t"
+        "mov.b16 m1, 0xBC00;\n\t"
+        "fma.rn.f32.f16 r0, h0, m1, %2;\n\t"
+        "fma.rn.f32.f16 r1, h1, m1, %3;\n\t"
+        "cvt.rn.f16x2.f32 %1, r1, r0;\n\t}"
+        : "=r"(hi), "=r"(lo)
+        : "f"(v0), "f"(v1));
+}
+
 // eight binary32 values -> binary16 hi and lo octets (16 bytes each)
 __device__ __forceinline__ void tc_split8(const float (&v)[8], uint4& hi, uint4& lo) {
     unsigned hw[4], lw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const __half2 hh = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-        const float2 hf = __half22float2(hh);
-        const __half2 ll = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
-        hw[j] = *reinterpret_cast<const unsigned*>(&hh);
-        lw[j] = *reinterpret_cast<const unsigned*>(&ll);
-    }
+    for (int j = 0; j < 4; ++j) tc_split2(v[2 * j], v[2 * j + 1], hw[j], lw[j]);
     hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
