@@ -153,6 +153,26 @@ __device__ __forceinline__ void kernel_pieces(const KernelPoly& kp, float u, flo
         for (int i = 0; i < W; ++i) v[i] = __fmaf_rn(v[i], u, kp.c[i][d]);
 }
 
+// The W kernel pieces at u from the first (W + 1) / 2 fits: the kernel is even, so piece W - 1 - i at
+// u equals piece i at -u.  With p_i(u) = E_i(u^2) + u O_i(u^2) both come from one evaluation of the
+// even and odd parts (Horner in u^2).
+template <int W>
+__device__ __forceinline__ void kernel_pieces_sym(const KernelPoly& kp, float u, float (&v)[W]) {
+    constexpr int DEG = poly_deg(W), NE = (DEG + 1) / 2, NO = DEG / 2;
+    const float u2 = u * u;
+#pragma unroll
+    for (int i = 0; i < (W + 1) / 2; ++i) {
+        float e = kp.c[i][2 * (NE - 1)];
+#pragma unroll
+        for (int k = NE - 2; k >= 0; --k) e = __fmaf_rn(e, u2, kp.c[i][2 * k]);
+        float o = kp.c[i][2 * (NO - 1) + 1];
+#pragma unroll
+        for (int k = NO - 2; k >= 0; --k) o = __fmaf_rn(o, u2, kp.c[i][2 * k + 1]);
+        v[i] = __fmaf_rn(u, o, e);
+        if (W - 1 - i != i) v[W - 1 - i] = __fmaf_rn(-u, o, e);
+    }
+}
+
 // Per-sample setup shared by spreading and interpolation (binary32 path): window test, first
 // node r0 of each dimension and the W kernel values there.  Returns false for samples outside
 // the window (or non-finite ones, which also latch ST_NONFINITE).
@@ -211,8 +231,8 @@ __device__ __forceinline__ bool prep_f32(const FastFrame& ff, const float4* __re
                                          float (&kx)[W], float (&ky)[W], unsigned* status) {
     float ax, ay;
     if (!prep_coords_f32<NF, W>(ff, edge, cc, px, py, r0x, r0y, ax, ay, status)) return false;
-    kernel_pieces<W>(kp, ax, kx);
-    kernel_pieces<W>(kp, ay, ky);
+    kernel_pieces_sym<W>(kp, ax, kx);
+    kernel_pieces_sym<W>(kp, ay, ky);
     return true;
 }
 
@@ -255,26 +275,6 @@ __device__ __forceinline__ void spread_taps(unsigned addr, const float (&kx)[W],
         } else {
             spread_taps<W, GS, J + 1, 0>(addr, kx, ky, c);
         }
-    }
-}
-
-// The W kernel pieces at u from the first (W + 1) / 2 fits: the kernel is even, so piece W - 1 - i at
-// u equals piece i at -u.  With p_i(u) = E_i(u^2) + u O_i(u^2) both come from one evaluation of the
-// even and odd parts (Horner in u^2).
-template <int W>
-__device__ __forceinline__ void kernel_pieces_sym(const KernelPoly& kp, float u, float (&v)[W]) {
-    constexpr int DEG = poly_deg(W), NE = (DEG + 1) / 2, NO = DEG / 2;
-    const float u2 = u * u;
-#pragma unroll
-    for (int i = 0; i < (W + 1) / 2; ++i) {
-        float e = kp.c[i][2 * (NE - 1)];
-#pragma unroll
-        for (int k = NE - 2; k >= 0; --k) e = __fmaf_rn(e, u2, kp.c[i][2 * k]);
-        float o = kp.c[i][2 * (NO - 1) + 1];
-#pragma unroll
-        for (int k = NO - 2; k >= 0; --k) o = __fmaf_rn(o, u2, kp.c[i][2 * k + 1]);
-        v[i] = __fmaf_rn(u, o, e);
-        if (W - 1 - i != i) v[W - 1 - i] = __fmaf_rn(-u, o, e);
     }
 }
 

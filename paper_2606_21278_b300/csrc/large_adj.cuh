@@ -239,8 +239,8 @@ static __global__ void __launch_bounds__(kLAdjThreads, 1) large_interp_kernel(co
                 continue;
             }
             float kx[W], ky[W];
-            kernel_pieces<W>(a.poly, ax, kx);
-            kernel_pieces<W>(a.poly, ay, ky);
+            kernel_pieces_sym<W>(a.poly, ax, kx);
+            kernel_pieces_sym<W>(a.poly, ay, ky);
             const float* gp = win + (r0y - rb) * kLWinCols + (r0x + kLWinShift);
             const float v = gather_taps<W, kLWinCols>(gp, kx, ky, 0.0f, 0.0f);
             const float ph = a.h[q], pw = a.w[q];
