@@ -338,7 +338,10 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = _rank_workload(args, ws, rank, "cuda")
-    plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame)
+    # n_f = 256 workloads take the subgrid tile the plan's tuner picks (16, 32 or 64 nodes), as their
+    # configuration prescribes; the others keep their prescribed routes
+    large = int(round(wl.sigma * wl.modes)) > 128
+    plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame, autotune=large)
     info = plan.info()
     prm = enufft.EMSParams()
     coeffs = plan.new_coeffs()
@@ -679,7 +682,7 @@ def run_ours(args):
                            **({"max_q": args.max_q} if args.max_q is not None else {}),
                            **({"cells_subset": args.cells} if args.cells is not None else {}),
                            "fine_grid": info["fine_grid"], "kernel_width": info["kernel_width"],
-                           "large_tile": info["large_tile"],
+                           "large_tile": info["large_tile"], **({"large_tile_from": "plan tuner"} if large else {}),
                            "kernel": args.kernel, "frame": args.frame, "precision": "mixed",
                            "ems": "K_max 12, alpha 0..0.7, delta 0.02, HEAD sums",
                            "timing": "one replay per step of the plan-owned CUDA graph of enufft_type1_ems (enufft_type1_ems_graph)",

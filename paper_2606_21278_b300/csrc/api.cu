@@ -873,6 +873,7 @@ static enufft_status run_large_batches(enufft_plan p, const void* x, const void*
     la.cell_exp = p->d_lexp;
     la.status = p->d_ctr + 2;
     la.poly = p->poly;
+    la.W = p->W;
     LargeFftArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.grid = reinterpret_cast<const long long*>(p->d_lgrid);

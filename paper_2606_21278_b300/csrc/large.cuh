@@ -46,19 +46,48 @@ __device__ __forceinline__ int large_tile_of(const CellConst& cc, float px, floa
 
 // 1. counting sort of one block's samples by tile (per-warp histograms, then a tile-major,
 // warp-minor prefix), records written inside the block's own range
+// Bank class of a sample in the spread's shared tile: the word of its first node modulo 32, from the
+// same plain binary32 coordinate as large_tile_of (only an ordering hint: a node off by one moves
+// the sample to another class, never to another result).
 template <int LT>
-__global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_constant__ LargeArgs a) {
+__device__ __forceinline__ int large_class_of(const CellConst& cc, int tile, int W, float px, float py) {
+    const int hs = W / 2 + 2, tstr = (LT + 2 * hs) | 1;
+    const float sx = (px - cc.cxh) * cc.sch + 0.5f * kLNF, sy = (py - cc.cyh) * cc.sch + 0.5f * kLNF;
+    const int r0x = (int)ceilf(sx - 0.5f * W), r0y = (int)ceilf(sy - 0.5f * W);
+    const int lx = r0x - ((tile % (kLNF / LT)) * LT - hs), ly = r0y - ((tile / (kLNF / LT)) * LT - hs);
+    return (ly * tstr + lx) & 31;
+}
+
+template <int LT>
+__global__ void __launch_bounds__(kLSortThreads, LT >= 32 ? 2 : 1) large_sort_kernel(const __grid_constant__ LargeArgs a) {
     constexpr int NT = kLSortThreads, PER = kLBinBlock / NT, NW = NT / 32, TT = large_tiles(LT);
+    // Inside each tile segment the records are written in rounds: round k holds the k-th record of
+    // every bank class present, classes ascending, so the 32 consecutive records one warp
+    // instruction of the spread takes mostly lie in different banks (IL; the first KM rounds, the
+    // rest after them).  The per-tile |c| sums keep the tile-major, warp-minor order.  Only the
+    // 64-node tiles take it: their segments (about 256 records of a sort block) fill the rounds,
+    // while the 64-record segments of 32-node tiles leave most rounds short (measured: 27.2 ms per
+    // step with 64-node tiles against 28.5 before; 32-node tiles 28.5 against 27.8 without it).
+    constexpr bool IL = LT >= 64;
+    constexpr int KM = 16;
     __shared__ int hist[NW][TT];
     __shared__ int toff[TT + 1];
-    __shared__ float cabs[kLBinBlock];   // |w h| / |D| in sorted order
+    __shared__ float cabs[kLBinBlock];   // |w h| / |D| in tile-major, warp-minor order
+    __shared__ int hc[IL ? TT * 32 : 1];                 // records per (tile, class)
+    __shared__ unsigned rmask[IL ? TT * KM : 1];         // classes present in round k of tile t
+    __shared__ int rstart[IL ? TT * (KM + 1) : 1];       // first position of round k in tile t
+    __shared__ int ovf[IL ? TT : 1];                     // records of tile t beyond round KM so far
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int4 blk = a.blocks[blockIdx.x];
     const CellConst& cc = a.cells[a.cell0 + blk.x];
     for (int i = tid; i < NW * TT; i += NT) (&hist[0][0])[i] = 0;
+    if constexpr (IL) {
+        for (int i = tid; i < TT * 32; i += NT) hc[i] = 0;
+        for (int i = tid; i < TT; i += NT) ovf[i] = 0;
+    }
     __syncthreads();
     float4 s[PER];
-    int tl[PER], rk[PER];
+    int tl[PER], rk[PER], kc[PER];   // tile; rank inside (warp, tile); rank inside (tile, class) << 5 | class
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int v = blk.y + tid + NT * i;
@@ -73,9 +102,29 @@ __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_
         if (blk.y + tid + NT * i < blk.z) {
             tl[i] = large_tile_of<LT>(cc, s[i].x, s[i].y);
             rk[i] = atomicAdd(&hist[warp][tl[i]], 1);
+            if constexpr (IL) {
+                const int c = large_class_of<LT>(cc, tl[i], a.W, s[i].x, s[i].y);
+                kc[i] = (atomicAdd(&hc[tl[i] * 32 + c], 1) << 5) | c;
+            }
         }
     }
     __syncthreads();
+    if constexpr (IL) {   // round tables: one warp per tile, lane = class
+        for (int t = warp; t < TT; t += NW) {
+            const int c = hc[t * 32 + lane];
+            int run = 0;
+#pragma unroll 1
+            for (int k = 0; k < KM; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, c > k);
+                if (lane == 0) {
+                    rmask[t * KM + k] = m;
+                    rstart[t * (KM + 1) + k] = run;
+                }
+                run += __popc(m);
+            }
+            if (lane == 0) rstart[t * (KM + 1) + KM] = run;
+        }
+    }
     if (tid < TT) {   // per tile: warp bases, then the tile's count
         int run = 0;
 #pragma unroll
@@ -124,8 +173,14 @@ __global__ void __launch_bounds__(kLSortThreads) large_sort_kernel(const __grid_
 #pragma unroll
     for (int i = 0; i < PER; ++i)
         if (tl[i] >= 0) {
-            const int slot = toff[tl[i]] + hist[warp][tl[i]] + rk[i];
-            a.rec[blk.y + slot] = s[i];
+            const int t = tl[i], slot = toff[t] + hist[warp][t] + rk[i];
+            int pos = slot;
+            if constexpr (IL) {
+                const int k = kc[i] >> 5, c = kc[i] & 31;
+                pos = toff[t] + (k < KM ? rstart[t * (KM + 1) + k] + __popc(rmask[t * KM + k] & ((1u << c) - 1u))
+                                        : rstart[t * (KM + 1) + KM] + atomicAdd(&ovf[t], 1));
+            }
+            a.rec[blk.y + pos] = s[i];
             const float v = fabsf(s[i].w * s[i].z) * inv_area;
             cabs[slot] = (v <= 3.0e38f) ? v : 0.0f;
         }

@@ -36,6 +36,7 @@ struct LargeArgs {
     int* cell_exp;                            // [ncells] k of each batch cell
     unsigned* status;
     KernelPoly poly;
+    int W;                                    // kernel width (the sort orders records by shared-memory bank)
 };
 
 constexpr int kLFftThreads = 512;
