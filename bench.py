@@ -341,7 +341,8 @@ def run_ours(args):
     # n_f = 256 workloads take the subgrid tile the plan's tuner picks (16, 32 or 64 nodes), as their
     # configuration prescribes; the others keep their prescribed routes
     large = int(round(wl.sigma * wl.modes)) > 128
-    plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame, autotune=large)
+    plan = enufft.Plan.for_workload(wl, kernel=args.kernel, frame=args.frame, autotune=large,
+                                    tune_cache=args.tune_cache if large else None)
     info = plan.info()
     prm = enufft.EMSParams()
     coeffs = plan.new_coeffs()
@@ -826,6 +827,8 @@ def main():
     ap.add_argument("--no-voronoi", action="store_true", help="skip timing the Voronoi quadrature weights")
     ap.add_argument("--no-gradient", action="store_true", help="skip timing the differentiation workload")
     ap.add_argument("--no-tune", action="store_true", help="skip timing the step with tuned routes")
+    ap.add_argument("--tune-cache", default=None,
+                    help="route-tuning cache file for the n_f = 256 tile choice (a second run reads it, no trial launches)")
     ap.add_argument("--check-cells", type=int, default=1024,
                     help="cells of the untimed parity check against the binary64 oracle")
     ap.add_argument("--kernel", default="es", choices=["es", "kb"],
