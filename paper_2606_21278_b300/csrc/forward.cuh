@@ -141,18 +141,6 @@ __device__ __forceinline__ int window_f32(const FastFrame& ff, const float4* __r
     return f > -tau ? -1 : 1;
 }
 
-// Horner evaluation of the W kernel pieces at u in [-1, 1] (DEG coefficients, compile time)
-template <int W>
-__device__ __forceinline__ void kernel_pieces(const KernelPoly& kp, float u, float (&v)[W]) {
-    constexpr int DEG = poly_deg(W);
-#pragma unroll
-    for (int i = 0; i < W; ++i) v[i] = kp.c[i][DEG - 1];
-#pragma unroll
-    for (int d = DEG - 2; d >= 0; --d)
-#pragma unroll
-        for (int i = 0; i < W; ++i) v[i] = __fmaf_rn(v[i], u, kp.c[i][d]);
-}
-
 // The W kernel pieces at u from the first (W + 1) / 2 fits: the kernel is even, so piece W - 1 - i at
 // u equals piece i at -u.  With p_i(u) = E_i(u^2) + u O_i(u^2) both come from one evaluation of the
 // even and odd parts (Horner in u^2).
@@ -262,20 +250,6 @@ __device__ __forceinline__ bool prep_f64(const CellConst& cc, const KernelPoly& 
 template <int OFF>
 __device__ __forceinline__ void red_smem(unsigned addr, int v) {
     asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF * 4));
-}
-
-// the W x W taps of one sample: c (already multiplied by the cell's fixed-point scale) times the
-// separable kernel, rounded to the nearest integer
-template <int W, int GS, int J = 0, int I = 0>
-__device__ __forceinline__ void spread_taps(unsigned addr, const float (&kx)[W], const float (&ky)[W], float c) {
-    if constexpr (J < W) {
-        if constexpr (I < W) {
-            red_smem<J * GS + I>(addr, __float2int_rn((c * ky[J]) * kx[I]));
-            spread_taps<W, GS, J, I + 1>(addr, kx, ky, c);
-        } else {
-            spread_taps<W, GS, J + 1, 0>(addr, kx, ky, c);
-        }
-    }
 }
 
 // Rounding to the nearest integer by one multiply-add: for |v| < 2^22, v + 1.5 * 2^23 lies in
@@ -408,23 +382,6 @@ __device__ __forceinline__ void spread_cell_f32(unsigned gaddr, int4* __restrict
             }
         }
     }
-}
-
-// spread one sample (binary32 path) into the fixed-point grid g (scale: the cell's 2^30 / S)
-template <int NF, int W, int GS, int HO>
-__device__ __forceinline__ void spread_f32(int* __restrict__ g, const FastFrame& ff, const float4* __restrict__ edge,
-                                           const CellConst& cc, const KernelPoly& kp, float px, float py, float ph,
-                                           float pw, float scale, unsigned* status) {
-    int r0x, r0y;
-    float kx[W], ky[W];
-    if (!prep_f32<NF, W>(ff, edge, cc, kp, px, py, r0x, r0y, kx, ky, status)) return;
-    const float c = pw * ph * ff.inv_area * scale;
-    if (!isfinite(c)) {
-        atomicOr(status, ST_NONFINITE);
-        return;
-    }
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(g + (r0y + HO) * GS + (r0x + HO));
-    spread_taps<W, GS>(addr, kx, ky, c);
 }
 
 // spread one sample (binary64 path)
