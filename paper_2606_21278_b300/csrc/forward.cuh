@@ -161,9 +161,6 @@ __device__ __forceinline__ void kernel_pieces_sym(const KernelPoly& kp, float u,
     }
 }
 
-// Per-sample setup shared by spreading and interpolation (binary32 path): window test, first
-// node r0 of each dimension and the W kernel values there.  Returns false for samples outside
-// the window (or non-finite ones, which also latch ST_NONFINITE).
 // The three-edge case of window_f32 (triangular cells), the edges held in registers.
 __device__ __forceinline__ int window_tri_f32(const FastFrame& ff, const float4& e0, const float4& e1, const float4& e2,
                                               float ux, float uy) {
@@ -175,7 +172,11 @@ __device__ __forceinline__ int window_tri_f32(const FastFrame& ff, const float4&
     return f > -ff.tau ? -1 : 1;
 }
 
-// prep_coords_f32 with the binary32 window test given by the caller (win(ux, uy) as window_f32)
+// Per-sample setup shared by spreading and interpolation (binary32 path): window test, first
+// node r0 of each dimension and the kernel argument there (prep_f32 adds the W kernel values).
+// Returns false for samples outside the window (or non-finite ones, which also latch
+// ST_NONFINITE).  This form takes the binary32 window test from the caller (win(ux, uy) as
+// window_f32); prep_coords_f32 below uses window_f32 itself.
 template <int NF, int W, typename Win>
 __device__ __forceinline__ bool prep_coords_win_f32(const FastFrame& ff, const Win& win_f32, const CellConst& cc,
                                                     float px, float py, int& r0x, int& r0y, float& argx, float& argy,
