@@ -122,6 +122,40 @@ def test_samples_on_window_boundary_follow_the_binary64_decision(nb):
     assert err.max() <= 1e-5, err
 
 
+@pytest.mark.parametrize("mask", [1, 2])
+def test_samples_on_square_and_disk_boundary_follow_the_binary64_decision(mask):
+    """Samples on (and within rounding of) the square's sides (mask 1) or the disk's circle (mask 2)
+    are kept or dropped exactly as the binary64 definition decides: the binary32 test's undecided
+    band (largest excess within the margin) goes to the binary64 test."""
+    wl = synth.make("tri20480_p64", seed=4, n_cells=2, q_scale=0.1, dtype=torch.float64)
+    wl.mask = mask
+    nv, verts = int(wl.nverts[0]), wl.verts[0].numpy()
+    fr = oracle.frame(nv, verts, eta=wl.eta, mask=mask)
+    H = fr["H"]
+    rng = np.random.default_rng(1)
+    a, b = int(wl.offsets[0]), int(wl.offsets[1])
+    n = min(200, b - a)
+    if mask == 1:   # a point on one of the four sides
+        s_ = rng.integers(0, 4, n)
+        t = rng.uniform(-H, H, n)
+        ux = np.where(s_ == 0, H, np.where(s_ == 1, -H, t))
+        uy = np.where(s_ == 2, H, np.where(s_ == 3, -H, t))
+    else:           # a point on the circle of radius H
+        th = rng.uniform(0.0, 2.0 * np.pi, n)
+        ux, uy = H * np.cos(th), H * np.sin(th)
+    ux = ux + rng.standard_normal(n) * 1e-7 * H
+    uy = uy + rng.standard_normal(n) * 1e-7 * H
+    wl.x[a:a + n] = torch.tensor(fr["cx"] + ux)
+    wl.y[a:a + n] = torch.tensor(fr["cy"] + uy)
+    wl32 = synth.Workload(**{**wl.__dict__, "x": wl.x.float(), "y": wl.y.float(), "h": wl.h.float(),
+                             "w": wl.w.float()})
+    win = oracle.window(nv, verts, wl32.x[a:a + n].numpy(), wl32.y[a:a + n].numpy(), eta=wl.eta, mask=mask)
+    assert 0 < win.sum() < n   # the placed samples fall on both sides of the boundary
+    _, c = _run_type1(wl32)
+    err = _rel_l2(c, oracle.type1(wl32))
+    assert err.max() <= 1e-5, err
+
+
 def test_nonfinite_samples_are_skipped_and_reported():
     wl = synth.make("tri20480_p64", seed=5, n_cells=3, q_scale=0.1)
     bad = int(wl.offsets[1]) + 3
